@@ -1,0 +1,90 @@
+/*
+ * afr_oracle.h -- CPU oracle of the adaptive frameless reconstruction path.
+ *
+ * TEST INFRASTRUCTURE. This is a plain, slow, step-by-step restatement of the
+ * reconstruction method of Dayal, Woolley, Watson and Luebke, "Adaptive
+ * Frameless Rendering" (sections 4, 4.1, 5.1, 5.2, 6.1, 6.2), written for
+ * checking the CUDA library, never for producing results. Only the tests, the
+ * smoke check and the benchmark's CPU-baseline leg call it. It shares no code,
+ * header, table or helper with the CUDA library.
+ *
+ * Arithmetic is double precision, except the reprojected position, whose
+ * floor decides the destination bin: it is taken in single precision with one
+ * rounding per operation (no contraction), as the CUDA path takes it.
+ *
+ * Ring layout (canonical, used for comparisons): for pixel p = y*W + x and
+ * slot k (0 = newest), field f of the sample is slot[((size_t)p*b + k)*AFO_NF + f]
+ * and its insertion sequence number is seq[(size_t)p*b + k].
+ */
+#ifndef AFR_ORACLE_H
+#define AFR_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { AFO_X = 0, AFO_Y, AFO_T, AFO_DEPTH, AFO_R, AFO_G, AFO_B, AFO_MX, AFO_MY, AFO_NF };
+/* reprojected (frame-view) record: x', y', t, r, g, b */
+enum { AFO_RX = 0, AFO_RY, AFO_RT, AFO_RR, AFO_RG, AFO_RB, AFO_NR };
+/* tile statistics record */
+enum { AFO_TN = 0, AFO_TEMPTY, AFO_TMEANL, AFO_TVARL, AFO_TGX, AFO_TGY, AFO_TGT, AFO_TU, AFO_NT };
+/* filter parameters theta */
+enum { AFO_ALPHA_S = 0, AFO_BETA_S, AFO_CLAMP_S, AFO_ALPHA_T, AFO_BETA_T, AFO_CLAMP_T, AFO_NP };
+
+/* Section 4: push a batch into the per-pixel deep-buffer queues. Returns the
+ * number of rejected samples. seq of sample i is seq0 + i. */
+int64_t afo_ingest(int W, int H, int b, int32_t *count, float *slot, uint32_t *seq,
+                   uint32_t seq0, int64_t n, const float *pos, const float *col,
+                   const float *mo);
+
+/* Sections 4 and 4.1: per-pixel age-weighted mean luminance and gradients.
+ * Lbar is NaN for an empty pixel. */
+void afo_gradients(int W, int H, int b, const int32_t *count, const float *slot,
+                   const uint32_t *seq, float t_now, double *Lbar, double *Gx,
+                   double *Gy, double *Gt);
+
+/* Sections 4, 4.2 and 6.1: per-tile statistics (AFO_NT doubles per tile,
+ * tiles in row-major order of a ceil(H/S)-by-ceil(W/S) grid). */
+void afo_tile_feedback(int W, int H, int b, int S, const int32_t *count,
+                       const float *slot, float t_now, const double *Gx,
+                       const double *Gy, const double *Gt, double m, double *out);
+
+/* Section 6.2: reproject every resident sample to t_now and bin it into a
+ * CSR frame view (bins row-major, within a bin by seq ascending). off has P+1
+ * entries, rec has cap*AFO_NR floats. Returns the number of binned samples
+ * (or -1 if cap is too small); *dropped gets the off-image count. */
+int64_t afo_reproject(int W, int H, int b, const int32_t *count, const float *slot,
+                      const uint32_t *seq, float t_now, uint32_t *off, float *rec,
+                      uint32_t *rseq, int64_t cap, int64_t *dropped);
+
+/* Section 5.1: filter widths from density and gradients (tile size S). */
+void afo_sigma(int W, int H, int b, int S, const int32_t *count, const double *Gx,
+               const double *Gy, const double *Gt, const double *theta,
+               double window, double eps, double *sig_s, double *sig_t);
+
+/* Sections 5.1 and 5.2: normalised space-time Gaussian gather over the
+ * integer disc of radius R. out has 4 doubles per pixel (r, g, b, W). If
+ * pixels != NULL only those n_pixels pixel indices are filtered (others left
+ * untouched). */
+void afo_filter(int W, int H, int R, const uint32_t *off, const float *rec,
+                float t_now, const double *sig_s, const double *sig_t,
+                const int64_t *pixels, int64_t n_pixels, double *out);
+
+/* The same sum written over all samples for every pixel, with no bins. */
+void afo_filter_brute(int W, int H, int R, int64_t n, const float *rec, float t_now,
+                      const double *sig_s, const double *sig_t, double *out);
+
+/* Adjoint of the filter and the width mapping for a loss with per-pixel
+ * gradient grad_rgb (3 doubles per pixel): gradient with respect to the
+ * colours of the frame-view records (3 doubles per record) and to theta. */
+void afo_backward(int W, int H, int b, int S, int R, const int32_t *count,
+                  const double *Gx, const double *Gy, const double *Gt,
+                  const double *theta, double window, double eps,
+                  const uint32_t *off, const float *rec, float t_now,
+                  const double *grad_rgb, double *grad_col, double *grad_theta);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
