@@ -1,0 +1,247 @@
+/*
+ * afr.h -- C ABI of the GB300 reconstruction path of adaptive frameless
+ * rendering (Dayal, Woolley, Watson and Luebke, "Adaptive Frameless
+ * Rendering").
+ *
+ * The library keeps, per context, the reconstructor's temporally deep buffer
+ * (section 4: a per-pixel queue of depth b), estimates space-time colour
+ * gradients from it (section 4.1), reprojects the buffered samples to the
+ * display time (section 6.2), filters every pixel with a space-time Gaussian
+ * whose widths follow local sample density and gradients (sections 5.1 and
+ * 5.2), returns per-tile statistics for the sampler (sections 4, 4.2, 6.1)
+ * and runs the adjoint of the filter for fitting its width mapping.
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named *_dev are device memory owned by the caller; pointers
+ *    named *_host are host memory owned by the caller. The context owns its
+ *    internal buffers and frees them in afr_destroy.
+ *  - Compute calls are asynchronous on the given stream and return argument
+ *    or call-order errors synchronously. Failures detected on the device
+ *    (a bounded wait that ran out, a failed internal check) are recorded in a
+ *    device status word that afr_get_status reads (it synchronises).
+ *  - Nothing throws across the ABI and there is no CPU fallback: when no
+ *    CUDA device is usable, afr_create returns AFR_ERR_CUDA.
+ *  - Calls on one context are not thread-safe; distinct contexts are
+ *    independent.
+ */
+#ifndef AFR_H
+#define AFR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define AFR_API __attribute__((visibility("default")))
+#else
+#define AFR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as the CUDA runtime's cudaStream_t; 0 is the legacy stream. */
+typedef struct CUstream_st *afr_stream_t;
+
+typedef enum {
+    AFR_OK = 0,
+    AFR_ERR_INVALID_ARG = 1,   /* a pointer, size or parameter out of range */
+    AFR_ERR_BAD_STATE = 2,     /* calls out of order (see each call) */
+    AFR_ERR_OOM = 3,           /* a device allocation failed */
+    AFR_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    AFR_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out */
+    AFR_ERR_DEVICE_CHECK = 6   /* a device-side consistency check failed */
+} AfrStatus;
+
+/* Storage type of buffered sample colours. Accumulation is always FP32. */
+typedef enum { AFR_F32 = 0, AFR_F16 = 1, AFR_BF16 = 2 } AfrColorType;
+
+typedef struct {
+    int32_t width, height;   /* image size in pixels, 1..16384 each */
+    int32_t depth;           /* b, queue depth per pixel, 1..32 (section 4 uses 4) */
+    int32_t tile;            /* S, side of the density/statistics tiles, 1..256 (default 32) */
+    int32_t radius;          /* R, filter footprint radius in bins, 0..8 (default 4) */
+    int32_t color_type;      /* AfrColorType */
+    float window;            /* length of the time window in its own units (default 1) */
+    float eps_grad;          /* floor of the gradients in the extent rule (default 1e-4) */
+    float undersample_m;     /* m of the undersampling measure (default 2) */
+} AfrConfig;
+
+/* Mapping from filter extents to Gaussian widths (theta). Section 5.1 sizes
+ * the extents; the widths are sigma_s = min(max(alpha_s e_s + beta_s, 0.5),
+ * clamp_s) in pixels and sigma_t = min(max(alpha_t e_t + beta_t, 0.05),
+ * clamp_t) in window units. Defaults 1, 0, 3, 1, 0, 1. */
+typedef struct {
+    float alpha_s, beta_s, clamp_s, alpha_t, beta_t, clamp_t;
+} AfrParams;
+
+/* One batch of samples in device memory, sample i in insertion order:
+ *   pos_dev[i]    float4 (x, y, t, depth): pixel units, t in window units
+ *   color_dev[i]  4 x float32 (r, g, b, unused) for AFR_F32 contexts, or
+ *                 4 x 16-bit (r, g, b, unused) in the context's colour type
+ *   motion_dev[i] float2 screen velocity in pixels per window
+ * Each array must be 16-byte aligned (8-byte for motion and 16-bit colours). */
+typedef struct {
+    const void *pos_dev;
+    const void *color_dev;
+    const void *motion_dev;
+} AfrSampleBatch;
+
+/* Per-tile statistics (sections 4, 4.2 and 6.1), tiles row-major over a
+ * ceil(height/S) x ceil(width/S) grid. */
+typedef struct {
+    uint32_t n;            /* buffered samples whose pixel lies in the tile */
+    uint32_t empty_slots;  /* tile pixels * b - n */
+    float mean_L;          /* age-weighted mean luminance (0 if n == 0) */
+    float var_L;           /* age-weighted luminance variance */
+    float mean_Gx, mean_Gy, mean_Gt;  /* mean gradients over non-empty pixels */
+    float u;               /* undersampling measure */
+} AfrTileStats;
+
+/* Counters read back by afr_query (synchronises the stream). */
+typedef struct {
+    uint64_t inserted;     /* samples offered to afr_insert_samples so far */
+    uint64_t rejected;     /* of those, rejected (non-finite or off-image) */
+    uint64_t resident;     /* samples in the deep buffer now */
+    uint64_t frame;        /* samples in the frame view of the last afr_reproject */
+    uint64_t dropped;      /* samples the last afr_reproject moved off-image */
+    uint64_t unsorted_bins;/* frame bins too full to order by sequence (see afr_reproject) */
+} AfrInfo;
+
+typedef struct AfrContext AfrContext;
+
+/* Creates a context on the current CUDA device and allocates its buffers
+ * (deep buffer, gradient and width maps, frame view sized for width*height*
+ * depth samples, tile records). Returns AFR_ERR_INVALID_ARG for a config out
+ * of range, AFR_ERR_OOM / AFR_ERR_CUDA on failure (nothing is leaked). */
+AFR_API AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out);
+
+/* Frees everything the context owns. Safe on NULL. Synchronises the device. */
+AFR_API void afr_destroy(AfrContext *ctx);
+
+/* Empties the deep buffer and restarts sequence numbering. */
+AFR_API AfrStatus afr_reset(AfrContext *ctx, afr_stream_t stream);
+
+/* Grows the context's ingest scratch to hold batches of up to n samples so
+ * that later afr_insert_samples calls do not allocate. */
+AFR_API AfrStatus afr_reserve(AfrContext *ctx, uint32_t n);
+
+/* Section 4 (deep buffer): pushes n samples, in index order, into the
+ * queues of the pixels that contain them. A sample whose x, y, t, colour or
+ * motion is not finite, or whose position lies outside [0,width) x
+ * [0,height), is rejected and counted. A queue keeps its b newest samples by
+ * insertion order; sample i of the batch gets sequence number
+ * inserted_so_far + i. Grows the ingest scratch if n exceeds what
+ * afr_reserve set aside (that growth allocates and synchronises).
+ * Invalidates gradients and the frame view. n = 0 is a no-op. */
+AFR_API AfrStatus afr_insert_samples(AfrContext *ctx, const AfrSampleBatch *batch, uint32_t n,
+                             afr_stream_t stream);
+
+/* Sections 4 and 4.1: per-pixel age-weighted mean luminance (weights
+ * exp(-3.47 a), a = max(0, t_now - t)), spatial gradients G_x, G_y (mean of
+ * the one-sided absolute luminance differences to the existing non-empty
+ * neighbours) and temporal gradient G_t (over the pixel's queue ordered by
+ * time, newest first: age-weighted sum of |dL| over consecutive samples
+ * divided by the age-weighted sum of their time steps), plus the per-tile
+ * partial statistics that afr_tile_feedback and afr_reconstruct read. */
+AFR_API AfrStatus afr_estimate_gradients(AfrContext *ctx, float t_now, afr_stream_t stream);
+
+/* Section 6.2: moves every buffered sample to t_now along its motion,
+ * x' = x + m_x (t_now - t) in single precision with one rounding per
+ * operation, and bins it at the pixel holding x' into the frame view.
+ * Samples leaving the image are dropped and counted. Within a bin, records
+ * are ordered by sequence number; a bin holding more than 4096 records keeps
+ * arrival order instead (counted in AfrInfo.unsorted_bins). */
+AFR_API AfrStatus afr_reproject(AfrContext *ctx, float t_now, afr_stream_t stream);
+
+/* Sections 5.1 and 5.2: for every pixel, the extents e_s = cbrt(V_S G_t/G_s),
+ * e_t = cbrt(V_S G_s^2/G_t^2) (V_S = tile pixels * window / tile samples,
+ * G_s = max((G_x+G_y)/2, eps), G_t floored at eps), the widths of AfrParams,
+ * and the normalised Gaussian-weighted mean of the frame-view samples whose
+ * bins lie within the integer disc of radius R around the pixel's bin:
+ * w = exp(-|x' - c|^2 / (2 sigma_s^2) - (t_now - t)^2 / (2 sigma_t^2)).
+ * out_rgbw_dev receives width*height float4 (r, g, b, W) row-major, W the
+ * weight sum; a pixel with no sample in its footprint gets (0, 0, 0, 0).
+ * Requires afr_estimate_gradients and afr_reproject for this t_now since the
+ * last insertion (else AFR_ERR_BAD_STATE). */
+AFR_API AfrStatus afr_reconstruct(AfrContext *ctx, float t_now, const AfrParams *params,
+                          float *out_rgbw_dev, afr_stream_t stream);
+
+/* Sections 4, 4.2, 6.1: writes one AfrTileStats per tile to out_dev, with
+ * u = 1 - min(1, m * mean_empty / empty) (0 for a tile with no empty slot).
+ * Requires afr_estimate_gradients since the last insertion. */
+AFR_API AfrStatus afr_tile_feedback(AfrContext *ctx, AfrTileStats *out_dev, afr_stream_t stream);
+
+/* Adjoint of afr_reconstruct (no counterpart in the paper, which does not
+ * differentiate its filter). grad_rgb_dev: width*height float4, the loss
+ * gradient with respect to each output (r, g, b); its 4th lane is ignored
+ * (W is treated as a constant). Writes grad_colors_dev (3 floats per
+ * frame-view record, frame order; AfrInfo.frame records) and grad_params_dev
+ * (6 floats, AfrParams order, summed in double precision). Gradients and
+ * densities are held fixed. Weight sums are recomputed, not stored. Requires
+ * a preceding afr_reconstruct on the current frame view; its params and
+ * t_now are reused. Either output pointer may be NULL to skip it. */
+AFR_API AfrStatus afr_reconstruct_backward(AfrContext *ctx, const float *grad_rgb_dev,
+                                   float *grad_colors_dev, float *grad_params_dev,
+                                   afr_stream_t stream);
+
+/* Synchronises the device and returns the first error recorded on it since
+ * the last call (and clears it), or AFR_OK. */
+AFR_API AfrStatus afr_get_status(AfrContext *ctx);
+
+/* Text of the most recent error on this context ("" if none). The pointer
+ * stays valid until the next call on the context. */
+AFR_API const char *afr_last_error(const AfrContext *ctx);
+
+/* Synchronises the stream and fills *info. */
+AFR_API AfrStatus afr_query(AfrContext *ctx, AfrInfo *info, afr_stream_t stream);
+
+/* Number of statistics tiles. */
+AFR_API AfrStatus afr_num_tiles(const AfrContext *ctx, uint32_t *n_tiles);
+
+/* ---------------------------------------------------------------------
+ * Inspection and injection (tests, checkpointing). All synchronise.
+ * --------------------------------------------------------------------- */
+
+/* Copies the deep buffer out in canonical order: for pixel p and k = 0
+ * (newest) .. count-1, fields x, y, t, depth, r, g, b, mx, my as float
+ * (slot_host[(p*depth + k)*9 + f], colours widened to float) and sequence
+ * number seq_host[p*depth + k]. count_host gets width*height int32. Slots
+ * past a pixel's count are zero. */
+AFR_API AfrStatus afr_export_ring(AfrContext *ctx, int32_t *count_host, float *slot_host,
+                          uint32_t *seq_host);
+
+/* Copies the frame view out: off_host (width*height+1 uint32), and per
+ * record (frame order) x', y', a^2 (a = t_now - t), r, g, b as float
+ * (rec_host, 6 per record) and the sequence number. cap is the record
+ * capacity of rec_host/seq_host; AFR_ERR_INVALID_ARG if the frame is larger. */
+AFR_API AfrStatus afr_export_frame(AfrContext *ctx, uint32_t *off_host, float *rec_host,
+                           uint32_t *seq_host, uint64_t cap);
+
+typedef enum {
+    AFR_MAP_LBAR = 0,   /* age-weighted mean luminance (NaN where empty) */
+    AFR_MAP_GX = 1, AFR_MAP_GY = 2, AFR_MAP_GT = 3,
+    AFR_MAP_SIGMA_S = 4, AFR_MAP_SIGMA_T = 5
+} AfrMap;
+
+/* Copies one width*height float map out / in. Importing a gradient map
+ * replaces the estimate (the next afr_reconstruct computes widths from it);
+ * importing a width map makes the next afr_reconstruct use it as is
+ * (AFR_RECON_KEEP_SIGMA). */
+AFR_API AfrStatus afr_export_map(AfrContext *ctx, AfrMap which, float *map_host);
+AFR_API AfrStatus afr_import_map(AfrContext *ctx, AfrMap which, const float *map_host);
+
+/* Replaces the colours of the frame view (3 floats per record, frame
+ * order, device memory), e.g. to differentiate with respect to them. */
+AFR_API AfrStatus afr_set_frame_colors(AfrContext *ctx, const float *rgb_dev, afr_stream_t stream);
+
+enum { AFR_RECON_KEEP_SIGMA = 1 };
+/* afr_reconstruct with flags: AFR_RECON_KEEP_SIGMA filters with the width
+ * map already in the context (imported or from the previous call). */
+AFR_API AfrStatus afr_reconstruct_ex(AfrContext *ctx, float t_now, const AfrParams *params,
+                             uint32_t flags, float *out_rgbw_dev, afr_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,197 @@
+"""Python binding of the reconstruction library (argument marshalling only).
+
+Every compute step runs in the CUDA kernels of libafr.so; torch only provides
+device memory and the current stream. The names follow the C ABI
+(include/afr.h), which cites the passage of the paper each call implements.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_COLOR_TYPES = {"f32": L.AFR_F32, "f16": L.AFR_F16, "bf16": L.AFR_BF16}
+_COLOR_DTYPES = {L.AFR_F32: torch.float32, L.AFR_F16: torch.float16, L.AFR_BF16: torch.bfloat16}
+DEFAULT_PARAMS = (1.0, 0.0, 3.0, 1.0, 0.0, 1.0)
+TILE_FIELDS = ("n", "empty_slots", "mean_L", "var_L", "mean_Gx", "mean_Gy", "mean_Gt", "u")
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _params(p) -> L.AfrParams:
+    if p is None:
+        p = DEFAULT_PARAMS
+    if isinstance(p, torch.Tensor):
+        p = p.detach().to("cpu", torch.float64).tolist()
+    return L.AfrParams(*[float(v) for v in p])
+
+
+class Reconstructor:
+    """One reconstruction context: the deep buffer of a width x height image
+    with queues of depth `depth`, and everything derived from it."""
+
+    def __init__(self, width: int, height: int, depth: int, *, tile: int = 32, radius: int = 4,
+                 color_type: str = "f32", window: float = 1.0, eps_grad: float = 1e-4,
+                 undersample_m: float = 2.0, device=None):
+        self.lib = L.load()
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.type != "cuda":
+            raise ValueError("the reconstruction library runs on CUDA devices only")
+        torch.cuda.set_device(self.device)
+        self.W, self.H, self.b, self.S, self.R = width, height, depth, tile, radius
+        self.ct = _COLOR_TYPES[color_type]
+        self.color_dtype = _COLOR_DTYPES[self.ct]
+        cfg = L.AfrConfig(width, height, depth, tile, radius, self.ct, window, eps_grad, undersample_m)
+        h = ctypes.c_void_p()
+        st = self.lib.afr_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != L.AFR_OK:
+            raise L.AfrError(st, "afr_create failed")
+        self.h = h
+        n = ctypes.c_uint32()
+        self._check(self.lib.afr_num_tiles(self.h, ctypes.byref(n)))
+        self.n_tiles = n.value
+
+    # -- plumbing ------------------------------------------------------------------
+    def _check(self, st: int):
+        if st != L.AFR_OK:
+            msg = self.lib.afr_last_error(self.h) if getattr(self, "h", None) else b""
+            raise L.AfrError(st, (msg or b"").decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.afr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- the path ------------------------------------------------------------------
+    def reset(self, stream=None):
+        self._check(self.lib.afr_reset(self.h, _stream(stream)))
+
+    def reserve(self, n: int):
+        self._check(self.lib.afr_reserve(self.h, n))
+
+    def insert(self, pos: torch.Tensor, color: torch.Tensor, motion: torch.Tensor, stream=None):
+        n = pos.shape[0]
+        for t, dt, cols in ((pos, torch.float32, 4), (color, self.color_dtype, 4), (motion, torch.float32, 2)):
+            if t.device != self.device or t.dtype != dt or not t.is_contiguous() or tuple(t.shape) != (n, cols):
+                raise ValueError(f"batch tensor must be contiguous {dt} [{n}, {cols}] on {self.device}")
+        batch = L.AfrSampleBatch(pos.data_ptr(), color.data_ptr(), motion.data_ptr())
+        self._check(self.lib.afr_insert_samples(self.h, ctypes.byref(batch), n, _stream(stream)))
+
+    def estimate_gradients(self, t_now: float = 1.0, stream=None):
+        self._check(self.lib.afr_estimate_gradients(self.h, t_now, _stream(stream)))
+
+    def reproject(self, t_now: float = 1.0, stream=None):
+        self._check(self.lib.afr_reproject(self.h, t_now, _stream(stream)))
+
+    def reconstruct(self, t_now: float = 1.0, params=None, out: torch.Tensor | None = None, flags: int = 0,
+                    stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.H, self.W, 4), dtype=torch.float32, device=self.device)
+        prm = _params(params)
+        self._check(self.lib.afr_reconstruct_ex(self.h, t_now, ctypes.byref(prm), flags, _ptr(out),
+                                                _stream(stream)))
+        return out
+
+    def tile_feedback(self, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Raw AfrTileStats records as a [n_tiles, 8] float32 tensor (fields n
+        and empty_slots hold uint32 bits; see decode_tiles)."""
+        if out is None:
+            out = torch.empty((self.n_tiles, 8), dtype=torch.float32, device=self.device)
+        self._check(self.lib.afr_tile_feedback(self.h, _ptr(out), _stream(stream)))
+        return out
+
+    def backward(self, grad_rgbw: torch.Tensor, want_colors: bool = True, want_params: bool = True,
+                 n_frame: int | None = None, stream=None):
+        grad_rgbw = grad_rgbw.contiguous()
+        gcol = gprm = None
+        if want_colors:
+            if n_frame is None:
+                n_frame = self.query(stream)["frame"]
+            gcol = torch.empty((max(n_frame, 1), 3), dtype=torch.float32, device=self.device)
+        if want_params:
+            gprm = torch.empty(6, dtype=torch.float32, device=self.device)
+        self._check(self.lib.afr_reconstruct_backward(self.h, _ptr(grad_rgbw), _ptr(gcol), _ptr(gprm),
+                                                      _stream(stream)))
+        if gcol is not None:
+            gcol = gcol[:n_frame]
+        return gcol, gprm
+
+    def set_frame_colors(self, rgb: torch.Tensor, stream=None):
+        rgb = rgb.to(self.device, torch.float32).contiguous()
+        self._check(self.lib.afr_set_frame_colors(self.h, _ptr(rgb), _stream(stream)))
+
+    # -- inspection ----------------------------------------------------------------
+    def status(self) -> int:
+        return self.lib.afr_get_status(self.h)
+
+    def query(self, stream=None) -> dict:
+        info = L.AfrInfo()
+        self._check(self.lib.afr_query(self.h, ctypes.byref(info), _stream(stream)))
+        return {f: getattr(info, f) for f, _ in L.AfrInfo._fields_}
+
+    def export_ring(self):
+        P, b = self.W * self.H, self.b
+        count = np.zeros(P, np.int32)
+        slot = np.zeros((P, b, 9), np.float32)
+        seq = np.zeros((P, b), np.uint32)
+        self._check(self.lib.afr_export_ring(self.h, count.ctypes.data, slot.ctypes.data, seq.ctypes.data))
+        return count, slot, seq
+
+    def export_frame(self):
+        info = self.query()
+        n = max(int(info["frame"]), 1)
+        off = np.zeros(self.W * self.H + 1, np.uint32)
+        rec = np.zeros((n, 6), np.float32)
+        seq = np.zeros(n, np.uint32)
+        self._check(self.lib.afr_export_frame(self.h, off.ctypes.data, rec.ctypes.data, seq.ctypes.data, n))
+        m = int(off[-1])
+        return off, rec[:m], seq[:m]
+
+    def export_map(self, which: int) -> np.ndarray:
+        out = np.zeros(self.W * self.H, np.float32)
+        self._check(self.lib.afr_export_map(self.h, which, out.ctypes.data))
+        return out
+
+    def import_map(self, which: int, arr):
+        a = np.ascontiguousarray(arr, np.float32).reshape(-1)
+        assert a.size == self.W * self.H
+        self._check(self.lib.afr_import_map(self.h, which, a.ctypes.data))
+
+
+def decode_tiles(raw: torch.Tensor) -> dict:
+    r = raw.detach().cpu().contiguous()
+    u = r.view(torch.int32)
+    out = {"n": u[:, 0].numpy().astype(np.uint32), "empty_slots": u[:, 1].numpy().astype(np.uint32)}
+    for k, f in enumerate(TILE_FIELDS[2:], start=2):
+        out[f] = r[:, k].numpy()
+    return out
+
+
+def to_device_batch(batch: dict, device, color_dtype=torch.float32):
+    """Upload a workload batch (numpy arrays pos/color/motion) as contiguous tensors."""
+    pos = torch.from_numpy(np.ascontiguousarray(batch["pos"], np.float32)).to(device)
+    col = torch.from_numpy(np.ascontiguousarray(batch["color"], np.float32)).to(device).to(color_dtype)
+    mo = torch.from_numpy(np.ascontiguousarray(batch["motion"], np.float32)).to(device)
+    return pos.contiguous(), col.contiguous(), mo.contiguous()

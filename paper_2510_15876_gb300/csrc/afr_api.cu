@@ -1,0 +1,474 @@
+// afr_api.cu -- the C ABI of include/afr.h: context life cycle, argument and
+// call-order checks, and the stream-ordered launch sequence of each call.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "afr_internal.cuh"
+
+using afr::grid_for;
+
+namespace {
+
+AfrStatus fail(AfrContext *c, AfrStatus st, const char *msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+AfrStatus cuda_fail(AfrContext *c, cudaError_t e, const char *where) {
+    if (c) {
+        c->err = std::string(where) + ": " + cudaGetErrorString(e);
+    }
+    return e == cudaErrorMemoryAllocation ? AFR_ERR_OOM : AFR_ERR_CUDA;
+}
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    return cudaMalloc(reinterpret_cast<void **>(p), n * sizeof(T));
+}
+
+void free_all(AfrContext *c) {
+    void *ptrs[] = {c->r_xy, c->r_mo, c->r_t, c->r_depth, c->r_seq, c->r_col, c->r_state, c->bin_of, c->idx,
+                    c->pcnt, c->poff, c->lbar, c->grad, c->pstat, c->sigma, c->amin2, c->tiles, c->fcnt,
+                    c->foff, c->fpos, c->fcol, c->scan_tmp, c->bgrad, c->bparam, c->dcount, c->derr};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// IEEE binary16 bits to float, from the format's definition.
+float half_to_float(uint16_t h) {
+    int sgn = (h >> 15) & 1, ex = (h >> 10) & 31, man = h & 1023;
+    float v;
+    if (ex == 0) v = std::ldexp((float)man, -24);
+    else if (ex == 31) v = man ? NAN : INFINITY;
+    else v = std::ldexp((float)(man + 1024), ex - 25);
+    return sgn ? -v : v;
+}
+
+float bf16_to_float(uint16_t h) {
+    uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+void widen_colors(int ct, const void *src, size_t i, float *dst3) {
+    if (ct == AFR_F32) {
+        const float *f = static_cast<const float *>(src) + 4 * i;
+        dst3[0] = f[0]; dst3[1] = f[1]; dst3[2] = f[2];
+    } else {
+        const uint16_t *h = static_cast<const uint16_t *>(src) + 4 * i;
+        for (int k = 0; k < 3; ++k) dst3[k] = ct == AFR_F16 ? half_to_float(h[k]) : bf16_to_float(h[k]);
+    }
+}
+
+}  // namespace
+
+namespace afr {
+namespace {
+__global__ void k_resident(const uint32_t *state, int P, unsigned long long *out) {
+    unsigned long long acc = 0;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) acc += state[p] & 0xFFFFu;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+}  // namespace
+cudaError_t launch_resident_count(AfrContext *c, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(c->dcount + CNT_RESIDENT, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    k_resident<<<grid_for(c->P, 256), 256, 0, s>>>(c->r_state, c->P, c->dcount + CNT_RESIDENT);
+    return cudaGetLastError();
+}
+}  // namespace afr
+
+extern "C" {
+
+AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
+    if (!cfg || !out) return AFR_ERR_INVALID_ARG;
+    *out = nullptr;
+    const AfrConfig &g = *cfg;
+    if (g.width < 1 || g.height < 1 || g.width > 16384 || g.height > 16384 || g.depth < 1 ||
+        g.depth > afr::kMaxDepth || g.tile < 1 || g.tile > 256 || g.radius < 0 || g.radius > 8 ||
+        g.color_type < AFR_F32 || g.color_type > AFR_BF16 || !(g.window > 0.f) || !std::isfinite(g.window) ||
+        !(g.eps_grad > 0.f) || !(g.undersample_m >= 0.f))
+        return AFR_ERR_INVALID_ARG;
+    if ((size_t)g.width * g.height * g.depth >= 0xFFFFFFFFull) return AFR_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return AFR_ERR_CUDA;
+    }
+    AfrContext *c = new (std::nothrow) AfrContext();
+    if (!c) return AFR_ERR_OOM;
+    c->cfg = g;
+    c->W = g.width;
+    c->H = g.height;
+    c->b = g.depth;
+    c->S = g.tile;
+    c->R = g.radius;
+    c->ct = g.color_type;
+    c->P = c->W * c->H;
+    c->ntx = (c->W + c->S - 1) / c->S;
+    c->nty = (c->H + c->S - 1) / c->S;
+    c->ntiles = c->ntx * c->nty;
+    c->nslots = (size_t)c->P * c->b;
+    c->csize = c->ct == AFR_F32 ? 16 : 8;
+    c->frame_cap = c->nslots;
+    c->scan_tmp_n = afr::scan_tmp_elems(c->P);
+    c->n_bblocks = afr::backward_blocks(c->W, c->H);
+    cudaError_t e = cudaSuccess;
+    size_t P = c->P, N = c->nslots;
+#define AFR_ALLOC(ptr, n)                           \
+    if (e == cudaSuccess) e = dalloc(&(ptr), (n));
+    AFR_ALLOC(c->r_xy, N);
+    AFR_ALLOC(c->r_mo, N);
+    AFR_ALLOC(c->r_t, N);
+    AFR_ALLOC(c->r_depth, N);
+    AFR_ALLOC(c->r_seq, N);
+    if (e == cudaSuccess) e = cudaMalloc(&c->r_col, N * c->csize);
+    AFR_ALLOC(c->r_state, P);
+    AFR_ALLOC(c->pcnt, P);
+    AFR_ALLOC(c->poff, P + 1);
+    AFR_ALLOC(c->lbar, P);
+    AFR_ALLOC(c->grad, P);
+    AFR_ALLOC(c->pstat, P);
+    AFR_ALLOC(c->sigma, P);
+    AFR_ALLOC(c->amin2, P);
+    AFR_ALLOC(c->tiles, (size_t)c->ntiles);
+    AFR_ALLOC(c->fcnt, P);
+    AFR_ALLOC(c->foff, P + 1);
+    AFR_ALLOC(c->fpos, 2 * N);
+    if (e == cudaSuccess) e = cudaMalloc(&c->fcol, 2 * N * c->csize);
+    AFR_ALLOC(c->scan_tmp, c->scan_tmp_n);
+    AFR_ALLOC(c->bgrad, 2 * P);
+    AFR_ALLOC(c->bparam, (size_t)c->n_bblocks * 6);
+    AFR_ALLOC(c->dcount, (size_t)afr::CNT_N);
+    AFR_ALLOC(c->derr, 1);
+#undef AFR_ALLOC
+    if (e == cudaSuccess) e = cudaMemset(c->r_state, 0, P * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(c->foff, 0, (P + 1) * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(c->dcount, 0, afr::CNT_N * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->derr, 0, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        AfrStatus st = e == cudaErrorMemoryAllocation ? AFR_ERR_OOM : AFR_ERR_CUDA;
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return st;
+    }
+    *out = c;
+    return AFR_OK;
+}
+
+void afr_destroy(AfrContext *c) {
+    if (!c) return;
+    cudaDeviceSynchronize();
+    free_all(c);
+    delete c;
+}
+
+AfrStatus afr_reset(AfrContext *c, afr_stream_t stream) {
+    if (!c) return AFR_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(c->r_state, 0, (size_t)c->P * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->dcount, 0, afr::CNT_N * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "afr_reset");
+    c->inserted = 0;
+    c->grads_valid = c->frame_valid = c->recon_valid = false;
+    c->err.clear();
+    return AFR_OK;
+}
+
+AfrStatus afr_reserve(AfrContext *c, uint32_t n) {
+    if (!c) return AFR_ERR_INVALID_ARG;
+    if (n <= c->batch_cap) return AFR_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(c, e, "afr_reserve");
+    if (c->bin_of) cudaFree(c->bin_of);
+    if (c->idx) cudaFree(c->idx);
+    c->bin_of = c->idx = nullptr;
+    c->batch_cap = 0;
+    e = dalloc(&c->bin_of, n);
+    if (e == cudaSuccess) e = dalloc(&c->idx, n);
+    if (e != cudaSuccess) {
+        if (c->bin_of) cudaFree(c->bin_of);
+        if (c->idx) cudaFree(c->idx);
+        c->bin_of = c->idx = nullptr;
+        cudaGetLastError();
+        return cuda_fail(c, e, "afr_reserve");
+    }
+    c->batch_cap = n;
+    return AFR_OK;
+}
+
+AfrStatus afr_insert_samples(AfrContext *c, const AfrSampleBatch *batch, uint32_t n, afr_stream_t stream) {
+    if (!c) return AFR_ERR_INVALID_ARG;
+    if (n == 0) return AFR_OK;
+    if (!batch || !batch->pos_dev || !batch->color_dev || !batch->motion_dev)
+        return fail(c, AFR_ERR_INVALID_ARG, "afr_insert_samples: null batch pointer");
+    if (!aligned(batch->pos_dev, 16) || !aligned(batch->color_dev, c->csize) || !aligned(batch->motion_dev, 8))
+        return fail(c, AFR_ERR_INVALID_ARG, "afr_insert_samples: misaligned batch array");
+    if (c->inserted + n > 0xFFFFFFFFull)
+        return fail(c, AFR_ERR_INVALID_ARG, "afr_insert_samples: sequence numbers exhausted; call afr_reset");
+    AfrStatus st = afr_reserve(c, n);
+    if (st != AFR_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = afr::launch_ingest(c, batch, n, (uint32_t)c->inserted, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "afr_insert_samples");
+    c->inserted += n;
+    c->grads_valid = c->frame_valid = c->recon_valid = false;
+    return AFR_OK;
+}
+
+AfrStatus afr_estimate_gradients(AfrContext *c, float t_now, afr_stream_t stream) {
+    if (!c) return AFR_ERR_INVALID_ARG;
+    if (!std::isfinite(t_now)) return fail(c, AFR_ERR_INVALID_ARG, "afr_estimate_gradients: t_now not finite");
+    cudaError_t e = afr::launch_gradients(c, t_now, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(c, e, "afr_estimate_gradients");
+    c->grads_valid = true;
+    c->grads_t = t_now;
+    c->recon_valid = false;
+    return AFR_OK;
+}
+
+AfrStatus afr_reproject(AfrContext *c, float t_now, afr_stream_t stream) {
+    if (!c) return AFR_ERR_INVALID_ARG;
+    if (!std::isfinite(t_now)) return fail(c, AFR_ERR_INVALID_ARG, "afr_reproject: t_now not finite");
+    cudaError_t e = afr::launch_reproject(c, t_now, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(c, e, "afr_reproject");
+    c->frame_valid = true;
+    c->frame_t = t_now;
+    c->recon_valid = false;
+    return AFR_OK;
+}
+
+static bool params_ok(const AfrParams *p) {
+    const float v[6] = {p->alpha_s, p->beta_s, p->clamp_s, p->alpha_t, p->beta_t, p->clamp_t};
+    for (float f : v)
+        if (!std::isfinite(f)) return false;
+    return p->clamp_s > 0.f && p->clamp_t > 0.f;
+}
+
+AfrStatus afr_reconstruct_ex(AfrContext *c, float t_now, const AfrParams *params, uint32_t flags,
+                             float *out_rgbw_dev, afr_stream_t stream) {
+    if (!c) return AFR_ERR_INVALID_ARG;
+    if (!params || !out_rgbw_dev || !aligned(out_rgbw_dev, 16))
+        return fail(c, AFR_ERR_INVALID_ARG, "afr_reconstruct: null or misaligned pointer");
+    if (!params_ok(params)) return fail(c, AFR_ERR_INVALID_ARG, "afr_reconstruct: parameters not finite/positive");
+    bool keep = (flags & AFR_RECON_KEEP_SIGMA) != 0;
+    if (!c->frame_valid || c->frame_t != t_now)
+        return fail(c, AFR_ERR_BAD_STATE, "afr_reconstruct: call afr_reproject for this t_now first");
+    if (!keep && (!c->grads_valid || c->grads_t != t_now))
+        return fail(c, AFR_ERR_BAD_STATE, "afr_reconstruct: call afr_estimate_gradients for this t_now first");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (!keep) e = afr::launch_sigma(c, params, s);
+    if (e == cudaSuccess) e = afr::launch_filter(c, t_now, reinterpret_cast<float4 *>(out_rgbw_dev), s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "afr_reconstruct");
+    c->recon_valid = true;
+    c->recon_t = t_now;
+    c->recon_params = *params;
+    c->sigma_imported = keep;
+    return AFR_OK;
+}
+
+AfrStatus afr_reconstruct(AfrContext *c, float t_now, const AfrParams *params, float *out_rgbw_dev,
+                          afr_stream_t stream) {
+    return afr_reconstruct_ex(c, t_now, params, 0u, out_rgbw_dev, stream);
+}
+
+AfrStatus afr_tile_feedback(AfrContext *c, AfrTileStats *out_dev, afr_stream_t stream) {
+    if (!c) return AFR_ERR_INVALID_ARG;
+    if (!out_dev) return fail(c, AFR_ERR_INVALID_ARG, "afr_tile_feedback: null output");
+    if (!c->grads_valid) return fail(c, AFR_ERR_BAD_STATE, "afr_tile_feedback: call afr_estimate_gradients first");
+    cudaError_t e = afr::launch_feedback(c, out_dev, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(c, e, "afr_tile_feedback");
+    return AFR_OK;
+}
+
+AfrStatus afr_reconstruct_backward(AfrContext *c, const float *grad_rgb_dev, float *grad_colors_dev,
+                                   float *grad_params_dev, afr_stream_t stream) {
+    if (!c) return AFR_ERR_INVALID_ARG;
+    if (!grad_rgb_dev || !aligned(grad_rgb_dev, 16))
+        return fail(c, AFR_ERR_INVALID_ARG, "afr_reconstruct_backward: null or misaligned grad_rgb");
+    if (!c->recon_valid || !c->frame_valid)
+        return fail(c, AFR_ERR_BAD_STATE, "afr_reconstruct_backward: call afr_reconstruct first");
+    if (grad_params_dev && (c->sigma_imported || !c->grads_valid))
+        return fail(c, AFR_ERR_BAD_STATE,
+                    "afr_reconstruct_backward: parameter gradients need widths computed from gradients");
+    cudaError_t e = afr::launch_backward(c, reinterpret_cast<const float4 *>(grad_rgb_dev), grad_colors_dev,
+                                         grad_params_dev, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(c, e, "afr_reconstruct_backward");
+    return AFR_OK;
+}
+
+AfrStatus afr_get_status(AfrContext *c) {
+    if (!c) return AFR_ERR_INVALID_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(c, e, "afr_get_status");
+    uint32_t w = 0;
+    e = cudaMemcpy(&w, c->derr, sizeof(w), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "afr_get_status");
+    if (w) {
+        cudaMemset(c->derr, 0, sizeof(uint32_t));
+        if (w & afr::ERR_TIMEOUT) return fail(c, AFR_ERR_TIMEOUT, "a bounded device-side wait ran out");
+        return fail(c, AFR_ERR_DEVICE_CHECK, "a device-side check failed");
+    }
+    return AFR_OK;
+}
+
+const char *afr_last_error(const AfrContext *c) { return c ? c->err.c_str() : "null context"; }
+
+AfrStatus afr_query(AfrContext *c, AfrInfo *info, afr_stream_t stream) {
+    if (!c || !info) return AFR_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = afr::launch_resident_count(c, s);
+    unsigned long long cnt[afr::CNT_N] = {0};
+    uint32_t frame = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, c->dcount, sizeof(cnt), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&frame, c->foff + c->P, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "afr_query");
+    info->inserted = c->inserted;
+    info->rejected = cnt[afr::CNT_REJECTED];
+    info->resident = cnt[afr::CNT_RESIDENT];
+    info->frame = c->frame_valid ? frame : 0;
+    info->dropped = cnt[afr::CNT_DROPPED];
+    info->unsorted_bins = cnt[afr::CNT_UNSORTED];
+    return AFR_OK;
+}
+
+AfrStatus afr_num_tiles(const AfrContext *c, uint32_t *n) {
+    if (!c || !n) return AFR_ERR_INVALID_ARG;
+    *n = (uint32_t)c->ntiles;
+    return AFR_OK;
+}
+
+AfrStatus afr_export_ring(AfrContext *c, int32_t *count_host, float *slot_host, uint32_t *seq_host) {
+    if (!c || !count_host || !slot_host || !seq_host) return AFR_ERR_INVALID_ARG;
+    size_t P = c->P, N = c->nslots;
+    std::vector<uint32_t> state(P), seq(N);
+    std::vector<float2> xy(N), mo(N);
+    std::vector<float> t(N), depth(N);
+    std::vector<unsigned char> col(N * c->csize);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(state.data(), c->r_state, P * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(seq.data(), c->r_seq, N * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(xy.data(), c->r_xy, N * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(mo.data(), c->r_mo, N * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(t.data(), c->r_t, N * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(depth.data(), c->r_depth, N * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(col.data(), c->r_col, N * c->csize, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "afr_export_ring");
+    std::memset(slot_host, 0, N * 9 * sizeof(float));
+    std::memset(seq_host, 0, N * sizeof(uint32_t));
+    for (size_t p = 0; p < P; ++p) {
+        int n = (int)(state[p] & 0xFFFFu), h = (int)(state[p] >> 16);
+        count_host[p] = n;
+        for (int k = 0; k < n; ++k) {
+            int s = h - 1 - k;
+            if (s < 0) s += c->b;
+            size_t i = p * c->b + s;
+            float *o = slot_host + (p * c->b + k) * 9;
+            o[0] = xy[i].x;
+            o[1] = xy[i].y;
+            o[2] = t[i];
+            o[3] = depth[i];
+            widen_colors(c->ct, col.data(), i, o + 4);
+            o[7] = mo[i].x;
+            o[8] = mo[i].y;
+            seq_host[p * c->b + k] = seq[i];
+        }
+    }
+    return AFR_OK;
+}
+
+AfrStatus afr_export_frame(AfrContext *c, uint32_t *off_host, float *rec_host, uint32_t *seq_host, uint64_t cap) {
+    if (!c || !off_host || !rec_host || !seq_host) return AFR_ERR_INVALID_ARG;
+    if (!c->frame_valid) return fail(c, AFR_ERR_BAD_STATE, "afr_export_frame: no frame view");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(off_host, c->foff, (size_t)(c->P + 1) * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "afr_export_frame");
+    size_t n = off_host[c->P];
+    if (n > cap) return fail(c, AFR_ERR_INVALID_ARG, "afr_export_frame: capacity too small");
+    std::vector<float4> pos(n ? n : 1);
+    std::vector<unsigned char> col((n ? n : 1) * c->csize);
+    if (n) {
+        e = cudaMemcpy(pos.data(), c->fpos, n * 16, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(col.data(), c->fcol, n * c->csize, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "afr_export_frame");
+    }
+    for (size_t i = 0; i < n; ++i) {
+        float *o = rec_host + i * 6;
+        o[0] = pos[i].x;
+        o[1] = pos[i].y;
+        o[2] = pos[i].z;
+        widen_colors(c->ct, col.data(), i, o + 3);
+        uint32_t sq;
+        std::memcpy(&sq, &pos[i].w, 4);
+        seq_host[i] = sq;
+    }
+    return AFR_OK;
+}
+
+AfrStatus afr_export_map(AfrContext *c, AfrMap which, float *map_host) {
+    if (!c || !map_host) return AFR_ERR_INVALID_ARG;
+    size_t P = c->P;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(c, e, "afr_export_map");
+    if (which == AFR_MAP_LBAR) {
+        e = cudaMemcpy(map_host, c->lbar, P * 4, cudaMemcpyDeviceToHost);
+    } else if (which >= AFR_MAP_GX && which <= AFR_MAP_GT) {
+        e = cudaMemcpy2D(map_host, 4, reinterpret_cast<float *>(c->grad) + (which - AFR_MAP_GX), 16, 4, P,
+                         cudaMemcpyDeviceToHost);
+    } else if (which == AFR_MAP_SIGMA_S || which == AFR_MAP_SIGMA_T) {
+        e = cudaMemcpy2D(map_host, 4, reinterpret_cast<float *>(c->sigma) + (which - AFR_MAP_SIGMA_S), 8, 4, P,
+                         cudaMemcpyDeviceToHost);
+    } else {
+        return fail(c, AFR_ERR_INVALID_ARG, "afr_export_map: unknown map");
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "afr_export_map");
+    return AFR_OK;
+}
+
+AfrStatus afr_import_map(AfrContext *c, AfrMap which, const float *map_host) {
+    if (!c || !map_host) return AFR_ERR_INVALID_ARG;
+    size_t P = c->P;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(c, e, "afr_import_map");
+    if (which == AFR_MAP_LBAR) {
+        e = cudaMemcpy(c->lbar, map_host, P * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2D(reinterpret_cast<float *>(c->grad) + 3, 16, map_host, 4, 4, P, cudaMemcpyHostToDevice);
+    } else if (which >= AFR_MAP_GX && which <= AFR_MAP_GT) {
+        e = cudaMemcpy2D(reinterpret_cast<float *>(c->grad) + (which - AFR_MAP_GX), 16, map_host, 4, 4, P,
+                         cudaMemcpyHostToDevice);
+    } else if (which == AFR_MAP_SIGMA_S || which == AFR_MAP_SIGMA_T) {
+        e = cudaMemcpy2D(reinterpret_cast<float *>(c->sigma) + (which - AFR_MAP_SIGMA_S), 8, map_host, 4, 4, P,
+                         cudaMemcpyHostToDevice);
+    } else {
+        return fail(c, AFR_ERR_INVALID_ARG, "afr_import_map: unknown map");
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "afr_import_map");
+    c->recon_valid = false;
+    return AFR_OK;
+}
+
+AfrStatus afr_set_frame_colors(AfrContext *c, const float *rgb_dev, afr_stream_t stream) {
+    if (!c || !rgb_dev) return AFR_ERR_INVALID_ARG;
+    if (!c->frame_valid) return fail(c, AFR_ERR_BAD_STATE, "afr_set_frame_colors: no frame view");
+    cudaError_t e = afr::launch_set_frame_colors(c, rgb_dev, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(c, e, "afr_set_frame_colors");
+    c->recon_valid = false;
+    return AFR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,199 @@
+// afr_internal.cuh -- context layout and device helpers shared by the CUDA
+// translation units of the reconstruction library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/afr.h"
+
+namespace afr {
+
+constexpr uint32_t kInvalid = 0xFFFFFFFFu;
+constexpr int kMaxDepth = 32;
+constexpr float kAgeDecay = 3.47f;               // section 4: exp(-3.47 a)
+constexpr float kLumR = 0.2126f, kLumG = 0.7152f, kLumB = 0.0722f;  // Rec. 709
+constexpr float kSigmaSMin = 0.5f, kSigmaTMin = 0.05f;
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr int kSortedBinMax = 4096;              // frame bins ordered by seq up to this size
+
+// device counters (unsigned long long)
+enum { CNT_REJECTED = 0, CNT_DROPPED, CNT_UNSORTED, CNT_RESIDENT, CNT_BIG, CNT_N };
+// device status word bits
+enum { ERR_TIMEOUT = 1u, ERR_CHECK = 2u };
+
+// Per-tile partial statistics written by the gradient pass.
+struct TilePartial {
+    double n;          // samples
+    double nonempty;   // non-empty pixels
+    double sw;         // sum of age weights
+    double mean;       // weighted mean luminance
+    double m2;         // weighted sum of squared deviations
+    double sgx, sgy, sgt;  // gradient sums over non-empty pixels
+};
+
+}  // namespace afr
+
+struct AfrContext {
+    AfrConfig cfg{};
+    int W = 0, H = 0, b = 0, S = 0, R = 0, ct = 0;
+    int P = 0;
+    int ntx = 0, nty = 0, ntiles = 0;
+    size_t nslots = 0;        // P * b
+    int csize = 16;           // bytes per stored colour (16 for F32, 8 for 16-bit)
+
+    // deep buffer, slot index p*b + s (storage order, circular per pixel)
+    float2 *r_xy = nullptr;
+    float2 *r_mo = nullptr;
+    float *r_t = nullptr;
+    float *r_depth = nullptr;
+    uint32_t *r_seq = nullptr;
+    void *r_col = nullptr;
+    uint32_t *r_state = nullptr;  // count | head << 16
+
+    // ingest scratch
+    uint32_t *bin_of = nullptr;   // [batch_cap]
+    uint32_t *idx = nullptr;      // [batch_cap]
+    size_t batch_cap = 0;
+    uint32_t *pcnt = nullptr;     // [P]
+    uint32_t *poff = nullptr;     // [P+1]
+
+    // maps
+    float *lbar = nullptr;        // [P]
+    float4 *grad = nullptr;       // [P] (Gx, Gy, Gt, Lbar)
+    float4 *pstat = nullptr;      // [P] (sum w, mean L, M2, Gt)
+    float2 *sigma = nullptr;      // [P] (sigma_s, sigma_t)
+    uint32_t *amin2 = nullptr;    // [P] float bits of min a^2 per frame bin
+    afr::TilePartial *tiles = nullptr;  // [ntiles]
+
+    // frame view
+    uint32_t *fcnt = nullptr;     // [P]
+    uint32_t *foff = nullptr;     // [P+1]
+    float4 *fpos = nullptr;       // [frame_cap] (x', y', a^2, seq bits)
+    void *fcol = nullptr;         // [frame_cap]
+    size_t frame_cap = 0;
+
+    // scan scratch
+    uint32_t *scan_tmp = nullptr;
+    size_t scan_tmp_n = 0;
+
+    // backward scratch
+    float4 *bgrad = nullptr;      // [P] per-pixel (g_r/S, g_g/S, g_b/S, valid)
+    double *bparam = nullptr;     // [n_bblocks * 6]
+    int n_bblocks = 0;
+
+    unsigned long long *dcount = nullptr;  // [CNT_N]
+    uint32_t *derr = nullptr;
+
+    // host-side state
+    uint64_t inserted = 0;
+    bool grads_valid = false;
+    float grads_t = 0.f;
+    bool frame_valid = false;
+    float frame_t = 0.f;
+    bool recon_valid = false;
+    float recon_t = 0.f;
+    AfrParams recon_params{};
+    bool sigma_imported = false;
+    std::string err;
+};
+
+namespace afr {
+
+// ---- colour storage ----------------------------------------------------------
+template <int CT> struct ColorStore;
+template <> struct ColorStore<AFR_F32> {
+    using T = float4;
+    static __device__ __forceinline__ float3 load(const void *base, size_t i) {
+        float4 v = __ldg(reinterpret_cast<const float4 *>(base) + i);
+        return make_float3(v.x, v.y, v.z);
+    }
+    static __device__ __forceinline__ T raw(const void *base, size_t i) {
+        return __ldg(reinterpret_cast<const float4 *>(base) + i);
+    }
+    static __device__ __forceinline__ float3 widen(T v) { return make_float3(v.x, v.y, v.z); }
+};
+template <> struct ColorStore<AFR_F16> {
+    using T = ushort4;
+    static __device__ __forceinline__ float3 widen(T v) {
+        return make_float3(__half2float(__ushort_as_half(v.x)), __half2float(__ushort_as_half(v.y)),
+                           __half2float(__ushort_as_half(v.z)));
+    }
+    static __device__ __forceinline__ T raw(const void *base, size_t i) {
+        return __ldg(reinterpret_cast<const ushort4 *>(base) + i);
+    }
+    static __device__ __forceinline__ float3 load(const void *base, size_t i) { return widen(raw(base, i)); }
+};
+template <> struct ColorStore<AFR_BF16> {
+    using T = ushort4;
+    static __device__ __forceinline__ float bf(unsigned short h) {
+        return __uint_as_float(((unsigned)h) << 16);
+    }
+    static __device__ __forceinline__ float3 widen(T v) { return make_float3(bf(v.x), bf(v.y), bf(v.z)); }
+    static __device__ __forceinline__ T raw(const void *base, size_t i) {
+        return __ldg(reinterpret_cast<const ushort4 *>(base) + i);
+    }
+    static __device__ __forceinline__ float3 load(const void *base, size_t i) { return widen(raw(base, i)); }
+};
+
+__device__ __forceinline__ float luminance(float3 c) {
+    return fmaf(kLumB, c.z, fmaf(kLumG, c.y, kLumR * c.x));
+}
+
+// 2^x with the hardware approximation (relative error below 2^-22).
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Warp-aggregated atomic add of 1 at base[key]: lanes with equal keys share
+// one atomic; returns this lane's ticket.
+__device__ __forceinline__ uint32_t agg_inc(uint32_t *base, uint32_t key) {
+    unsigned mask = __activemask();
+    unsigned peers = __match_any_sync(mask, key);
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(peers) - 1;
+    uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+    uint32_t first = 0;
+    if (lane == leader) first = atomicAdd(base + key, (uint32_t)__popc(peers));
+    first = __shfl_sync(peers, first, leader);
+    return first + rank;
+}
+
+// Warp-aggregated count of lanes with flag set, added to *ctr.
+__device__ __forceinline__ void agg_count(unsigned long long *ctr, bool flag) {
+    unsigned mask = __activemask();
+    unsigned bits = __ballot_sync(mask, flag);
+    if ((threadIdx.x & 31) == __ffs(mask) - 1 && bits) atomicAdd(ctr, (unsigned long long)__popc(bits));
+}
+
+inline int grid_for(size_t n, int block, int cap = 152 * 32) {
+    size_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > (size_t)cap) g = cap;
+    return (int)g;
+}
+
+// ---- launch wrappers (one per translation unit) ------------------------------
+// Each returns cudaSuccess or the launch error.
+cudaError_t scan_exclusive(const uint32_t *in, uint32_t *out, size_t n, uint32_t *tmp, cudaStream_t s);
+size_t scan_tmp_elems(size_t n);
+
+cudaError_t launch_ingest(AfrContext *c, const AfrSampleBatch *batch, uint32_t n, uint32_t seq0,
+                          cudaStream_t s);
+cudaError_t launch_gradients(AfrContext *c, float t_now, cudaStream_t s);
+cudaError_t launch_reproject(AfrContext *c, float t_now, cudaStream_t s);
+cudaError_t launch_sigma(AfrContext *c, const AfrParams *prm, cudaStream_t s);
+cudaError_t launch_filter(AfrContext *c, float t_now, float4 *out, cudaStream_t s);
+cudaError_t launch_feedback(AfrContext *c, AfrTileStats *out, cudaStream_t s);
+cudaError_t launch_backward(AfrContext *c, const float4 *grad_rgb, float *grad_col, float *grad_prm,
+                            cudaStream_t s);
+cudaError_t launch_set_frame_colors(AfrContext *c, const float *rgb, cudaStream_t s);
+int backward_blocks(int W, int H);
+cudaError_t launch_resident_count(AfrContext *c, cudaStream_t s);
+
+}  // namespace afr

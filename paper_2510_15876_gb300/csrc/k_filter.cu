@@ -1,0 +1,362 @@
+// k_filter.cu -- sections 5.1 and 5.2: filter widths from density and
+// gradients, the normalised space-time Gaussian gather over each pixel's
+// integer disc of frame bins, and its adjoint.
+//
+// Exponent shift. Every weight is 2^-E with E = d^2 ks + a^2 kt >= 0
+// (ks = log2 e / (2 sigma_s^2), kt = log2 e / (2 sigma_t^2)). A pixel whose
+// samples are all old under a narrow temporal filter has every E far above
+// the FP32 range, so the kernel subtracts a per-pixel shift m: the minimum
+// over the footprint's bins of a lower bound of E in that bin (the bin's
+// nearest point to the pixel centre and its smallest a^2). Then E - m >= 0
+// for every sample and E - m <= ((R+1)^2 - R^2 + ...) ks stays small for
+// the sample that attains the bound, so the normalised colour is exact up to
+// rounding whatever the ages; W is reported as S * 2^-m.
+#include "afr_internal.cuh"
+
+namespace afr {
+namespace {
+
+struct Widths {
+    float es, et, raw_s, raw_t, ss, st;
+};
+
+__device__ __forceinline__ Widths widths(float4 g, float V, float eps, const AfrParams &prm) {
+    Widths w;
+    float Gs = fmaxf(0.5f * (g.x + g.y), eps);
+    float Gt = fmaxf(g.z, eps);
+    w.es = cbrtf(V * Gt / Gs);
+    w.et = cbrtf(V * (Gs * Gs) / (Gt * Gt));
+    w.raw_s = fmaf(prm.alpha_s, w.es, prm.beta_s);
+    w.raw_t = fmaf(prm.alpha_t, w.et, prm.beta_t);
+    w.ss = fminf(fmaxf(w.raw_s, kSigmaSMin), prm.clamp_s);
+    w.st = fminf(fmaxf(w.raw_t, kSigmaTMin), prm.clamp_t);
+    return w;
+}
+
+__device__ __forceinline__ float tile_volume(int x, int y, int W, int H, int S, int ntx, float window,
+                                             const TilePartial *__restrict__ tiles) {
+    int tx = x / S, ty = y / S;
+    float A = (float)(min(S, W - tx * S) * min(S, H - ty * S));
+    float n = (float)__ldg(&tiles[ty * ntx + tx].n);
+    return n > 0.f ? A * window / n : A * window;
+}
+
+__global__ void __launch_bounds__(256) k_sigma(int W, int H, int S, int ntx, float window, float eps, AfrParams prm,
+                                               const float4 *__restrict__ grad, const TilePartial *__restrict__ tiles,
+                                               float2 *__restrict__ sigma) {
+    int P = W * H;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        int x = p % W, y = p / W;
+        Widths w = widths(__ldg(grad + p), tile_volume(x, y, W, H, S, ntx, window, tiles), eps, prm);
+        sigma[p] = make_float2(w.ss, w.st);
+    }
+}
+
+__device__ __forceinline__ int half_width(int R, int dy) {
+    int h = 0;
+    while ((h + 1) * (h + 1) + dy * dy <= R * R) ++h;
+    return h;
+}
+
+__device__ __forceinline__ float bin_gap(int d) {   // nearest distance from a pixel centre to a bin d away
+    float g = fabsf((float)d) - 0.5f;
+    return g > 0.f ? g : 0.f;
+}
+
+struct PixelFrame {
+    float cx, cy, ks, kt, m;
+    bool any;
+};
+
+// Per-pixel constants of the gather: centre, exponent scales and shift.
+__device__ __forceinline__ PixelFrame pixel_frame(int x, int y, int W, int H, int R, float2 sg,
+                                                  const uint32_t *__restrict__ amin2) {
+    PixelFrame f;
+    f.cx = (float)x + 0.5f;
+    f.cy = (float)y + 0.5f;
+    f.ks = kLog2e / (2.f * sg.x * sg.x);
+    f.kt = kLog2e / (2.f * sg.y * sg.y);
+    float m = INFINITY;
+    for (int dy = -R; dy <= R; ++dy) {
+        int row = y + dy;
+        if (row < 0 || row >= H) continue;
+        int hw = half_width(R, dy);
+        int x0 = max(0, x - hw), x1 = min(W - 1, x + hw);
+        float gy = bin_gap(dy);
+        for (int bx = x0; bx <= x1; ++bx) {
+            uint32_t a2 = __ldg(amin2 + (size_t)row * W + bx);
+            if (a2 == 0x7f800000u) continue;   // empty bin
+            float gx = bin_gap(bx - x);
+            float lb = fmaf(fmaf(gx, gx, gy * gy), f.ks, __uint_as_float(a2) * f.kt);
+            m = fminf(m, lb);
+        }
+    }
+    f.any = m < INFINITY;
+    f.m = f.any ? m : 0.f;
+    return f;
+}
+
+__device__ __forceinline__ float shifted_exponent(const PixelFrame &f, float4 r) {
+    float dx = r.x - f.cx, dy = r.y - f.cy;
+    float d2 = fmaf(dx, dx, dy * dy);
+    return fmaf(d2, f.ks, fmaf(r.z, f.kt, -f.m));
+}
+
+template <int CT, bool KAHAN>
+__global__ void __launch_bounds__(128) k_filter(int W, int H, int R, const float2 *__restrict__ sigma,
+                                                const uint32_t *__restrict__ amin2, const uint32_t *__restrict__ foff,
+                                                const float4 *__restrict__ fpos, const void *__restrict__ fcol,
+                                                float4 *__restrict__ out) {
+    using CS = ColorStore<CT>;
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= W || y >= H) return;
+    size_t p = (size_t)y * W + x;
+    PixelFrame f = pixel_frame(x, y, W, H, R, __ldg(sigma + p), amin2);
+    if (!f.any) {
+        out[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    float S = 0.f, cS = 0.f, sr = 0.f, sg = 0.f, sb = 0.f;
+    for (int dy = -R; dy <= R; ++dy) {
+        int row = y + dy;
+        if (row < 0 || row >= H) continue;
+        int hw = half_width(R, dy);
+        int x0 = max(0, x - hw), x1 = min(W - 1, x + hw);
+        uint32_t e0 = __ldg(foff + (size_t)row * W + x0), e1 = __ldg(foff + (size_t)row * W + x1 + 1);
+        for (uint32_t e = e0; e < e1; ++e) {
+            float4 r = __ldg(fpos + e);
+            float3 c = CS::load(fcol, e);
+            float w = ex2(-shifted_exponent(f, r));
+            if (KAHAN) {
+                float yk = w - cS;
+                float tk = S + yk;
+                cS = (tk - S) - yk;
+                S = tk;
+            } else {
+                S += w;
+            }
+            sr = fmaf(w, c.x, sr);
+            sg = fmaf(w, c.y, sg);
+            sb = fmaf(w, c.z, sb);
+        }
+    }
+    float inv = 1.f / S;
+    out[p] = make_float4(sr * inv, sg * inv, sb * inv, S * ex2(-f.m));
+}
+
+// ---- adjoint -------------------------------------------------------------------
+
+template <int CT>
+__global__ void __launch_bounds__(128) k_bwd_pixel(int W, int H, int R, int S_, int ntx, float window, float eps,
+                                                   AfrParams prm, const float4 *__restrict__ grad,
+                                                   const TilePartial *__restrict__ tiles,
+                                                   const float2 *__restrict__ sigma, const uint32_t *__restrict__ amin2,
+                                                   const uint32_t *__restrict__ foff, const float4 *__restrict__ fpos,
+                                                   const void *__restrict__ fcol, const float4 *__restrict__ gout,
+                                                   float4 *__restrict__ bg, float4 *__restrict__ bframe,
+                                                   double *__restrict__ bparam) {
+    using CS = ColorStore<CT>;
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    float gp[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (x < W && y < H) {
+        size_t p = (size_t)y * W + x;
+        float2 sgm = __ldg(sigma + p);
+        PixelFrame f = pixel_frame(x, y, W, H, R, sgm, amin2);
+        float4 g = __ldg(gout + p);
+        if (!f.any) {
+            bg[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+            bframe[p] = make_float4(f.ks, f.kt, f.m, 0.f);
+        } else {
+            float S = 0.f, sc[3] = {0.f, 0.f, 0.f}, Ds = 0.f, dsc[3] = {0.f, 0.f, 0.f}, Dt = 0.f,
+                  dtc[3] = {0.f, 0.f, 0.f};
+            for (int dy = -R; dy <= R; ++dy) {
+                int row = y + dy;
+                if (row < 0 || row >= H) continue;
+                int hw = half_width(R, dy);
+                int x0 = max(0, x - hw), x1 = min(W - 1, x + hw);
+                uint32_t e0 = __ldg(foff + (size_t)row * W + x0), e1 = __ldg(foff + (size_t)row * W + x1 + 1);
+                for (uint32_t e = e0; e < e1; ++e) {
+                    float4 r = __ldg(fpos + e);
+                    float3 c = CS::load(fcol, e);
+                    float w = ex2(-shifted_exponent(f, r));
+                    float ddx = r.x - f.cx, ddy = r.y - f.cy;
+                    float d2 = fmaf(ddx, ddx, ddy * ddy);
+                    float ws = w * d2, wt = w * r.z;
+                    S += w;
+                    sc[0] = fmaf(w, c.x, sc[0]); sc[1] = fmaf(w, c.y, sc[1]); sc[2] = fmaf(w, c.z, sc[2]);
+                    Ds += ws; Dt += wt;
+                    dsc[0] = fmaf(ws, c.x, dsc[0]); dsc[1] = fmaf(ws, c.y, dsc[1]); dsc[2] = fmaf(ws, c.z, dsc[2]);
+                    dtc[0] = fmaf(wt, c.x, dtc[0]); dtc[1] = fmaf(wt, c.y, dtc[1]); dtc[2] = fmaf(wt, c.z, dtc[2]);
+                }
+            }
+            float inv = 1.f / S;
+            float gch[3] = {g.x, g.y, g.z};
+            float s3 = sgm.x * sgm.x * sgm.x, t3 = sgm.y * sgm.y * sgm.y;
+            float gs = 0.f, gt = 0.f;
+            for (int ch = 0; ch < 3; ++ch) {
+                float C = sc[ch] * inv;
+                gs = fmaf(gch[ch], (dsc[ch] - C * Ds) * inv / s3, gs);
+                gt = fmaf(gch[ch], (dtc[ch] - C * Dt) * inv / t3, gt);
+            }
+            bg[p] = make_float4(g.x * inv, g.y * inv, g.z * inv, 1.f);
+            bframe[p] = make_float4(f.ks, f.kt, f.m, 1.f);
+            // chain through the width mapping; the widths depend on theta only
+            Widths wd = widths(__ldg(grad + p), tile_volume(x, y, W, H, S_, ntx, window, tiles), eps, prm);
+            if (fmaxf(wd.raw_s, kSigmaSMin) >= prm.clamp_s) gp[2] = gs;
+            else if (wd.raw_s > kSigmaSMin) { gp[0] = gs * wd.es; gp[1] = gs; }
+            if (fmaxf(wd.raw_t, kSigmaTMin) >= prm.clamp_t) gp[5] = gt;
+            else if (wd.raw_t > kSigmaTMin) { gp[3] = gt * wd.et; gp[4] = gt; }
+        }
+    }
+    // block reduction of the six parameter gradients, then one FP64 partial per block
+    __shared__ float sh[6][4];
+    int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int k = 0; k < 6; ++k) {
+        float v = gp[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) sh[k][tid >> 5] = v;
+    }
+    __syncthreads();
+    if (tid < 6) {
+        double acc = 0.0;
+        for (int w = 0; w < 4; ++w) acc += (double)sh[tid][w];
+        bparam[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 6 + tid] = acc;
+    }
+}
+
+// Gradient of each frame record's colour: sum over the pixels whose disc
+// holds the record's bin of (dL/dC_p / S_p) * shifted weight.
+__global__ void __launch_bounds__(256) k_bwd_record(int W, int H, int R, const uint32_t *__restrict__ foff,
+                                                    const float4 *__restrict__ fpos, const float4 *__restrict__ bg,
+                                                    const float4 *__restrict__ bframe, float *__restrict__ gcol) {
+    uint32_t n = __ldg(foff + (size_t)W * H);
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        float4 r = __ldg(fpos + e);
+        int qx = (int)floorf(r.x), qy = (int)floorf(r.y);
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+        for (int dy = -R; dy <= R; ++dy) {
+            int y = qy + dy;
+            if (y < 0 || y >= H) continue;
+            int hw = half_width(R, dy);
+            for (int x = max(0, qx - hw); x <= min(W - 1, qx + hw); ++x) {
+                size_t p = (size_t)y * W + x;
+                float4 fr = __ldg(bframe + p);
+                if (fr.w == 0.f) continue;
+                PixelFrame f;
+                f.cx = (float)x + 0.5f;
+                f.cy = (float)y + 0.5f;
+                f.ks = fr.x;
+                f.kt = fr.y;
+                f.m = fr.z;
+                float w = ex2(-shifted_exponent(f, r));
+                float4 g = __ldg(bg + p);
+                a0 = fmaf(g.x, w, a0);
+                a1 = fmaf(g.y, w, a1);
+                a2 = fmaf(g.z, w, a2);
+            }
+        }
+        gcol[3 * (size_t)e] = a0;
+        gcol[3 * (size_t)e + 1] = a1;
+        gcol[3 * (size_t)e + 2] = a2;
+    }
+}
+
+__global__ void k_bwd_params(const double *__restrict__ part, int nblocks, float *__restrict__ out) {
+    int k = threadIdx.x;
+    if (k >= 6) return;
+    double acc = 0.0;
+    for (int i = 0; i < nblocks; ++i) acc += part[(size_t)i * 6 + k];
+    out[k] = (float)acc;
+}
+
+template <int CT>
+__global__ void k_set_colors(const float *__restrict__ rgb, const uint32_t *__restrict__ foff, int P,
+                             void *__restrict__ fcol) {
+    uint32_t n = __ldg(foff + P);
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        float r = rgb[3 * (size_t)e], g = rgb[3 * (size_t)e + 1], b = rgb[3 * (size_t)e + 2];
+        if (CT == AFR_F32) {
+            reinterpret_cast<float4 *>(fcol)[e] = make_float4(r, g, b, 0.f);
+        } else if (CT == AFR_F16) {
+            reinterpret_cast<ushort4 *>(fcol)[e] = make_ushort4(__half_as_ushort(__float2half_rn(r)),
+                                                                __half_as_ushort(__float2half_rn(g)),
+                                                                __half_as_ushort(__float2half_rn(b)), 0);
+        } else {
+            reinterpret_cast<ushort4 *>(fcol)[e] = make_ushort4(__bfloat16_as_ushort(__float2bfloat16_rn(r)),
+                                                                __bfloat16_as_ushort(__float2bfloat16_rn(g)),
+                                                                __bfloat16_as_ushort(__float2bfloat16_rn(b)), 0);
+        }
+    }
+}
+
+const dim3 kFilterBlock(32, 4);
+
+}  // namespace
+
+cudaError_t launch_sigma(AfrContext *c, const AfrParams *prm, cudaStream_t s) {
+    k_sigma<<<grid_for(c->P, 256), 256, 0, s>>>(c->W, c->H, c->S, c->ntx, c->cfg.window, c->cfg.eps_grad, *prm,
+                                                c->grad, c->tiles, c->sigma);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_filter(AfrContext *c, float t_now, float4 *out, cudaStream_t s) {
+    (void)t_now;
+    dim3 grid((c->W + kFilterBlock.x - 1) / kFilterBlock.x, (c->H + kFilterBlock.y - 1) / kFilterBlock.y);
+    switch (c->ct) {
+        case AFR_F32:
+            k_filter<AFR_F32, false><<<grid, kFilterBlock, 0, s>>>(c->W, c->H, c->R, c->sigma, c->amin2, c->foff,
+                                                                   c->fpos, c->fcol, out);
+            break;
+        case AFR_F16:
+            k_filter<AFR_F16, true><<<grid, kFilterBlock, 0, s>>>(c->W, c->H, c->R, c->sigma, c->amin2, c->foff,
+                                                                  c->fpos, c->fcol, out);
+            break;
+        default:
+            k_filter<AFR_BF16, true><<<grid, kFilterBlock, 0, s>>>(c->W, c->H, c->R, c->sigma, c->amin2, c->foff,
+                                                                   c->fpos, c->fcol, out);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backward(AfrContext *c, const float4 *grad_rgb, float *grad_col, float *grad_prm,
+                            cudaStream_t s) {
+    dim3 grid((c->W + kFilterBlock.x - 1) / kFilterBlock.x, (c->H + kFilterBlock.y - 1) / kFilterBlock.y);
+    float4 *bframe = c->bgrad + c->P;
+    const AfrParams &prm = c->recon_params;
+#define AFR_BWD(CT_)                                                                                        \
+    k_bwd_pixel<CT_><<<grid, kFilterBlock, 0, s>>>(c->W, c->H, c->R, c->S, c->ntx, c->cfg.window,           \
+                                                   c->cfg.eps_grad, prm, c->grad, c->tiles, c->sigma, c->amin2, \
+                                                   c->foff, c->fpos, c->fcol, grad_rgb, c->bgrad, bframe,   \
+                                                   c->bparam)
+    switch (c->ct) {
+        case AFR_F32: AFR_BWD(AFR_F32); break;
+        case AFR_F16: AFR_BWD(AFR_F16); break;
+        default: AFR_BWD(AFR_BF16); break;
+    }
+#undef AFR_BWD
+    if (grad_col)
+        k_bwd_record<<<grid_for((size_t)c->P * c->b, 256), 256, 0, s>>>(c->W, c->H, c->R, c->foff, c->fpos, c->bgrad,
+                                                                        bframe, grad_col);
+    if (grad_prm) k_bwd_params<<<1, 32, 0, s>>>(c->bparam, (int)(grid.x * grid.y), grad_prm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_frame_colors(AfrContext *c, const float *rgb, cudaStream_t s) {
+    int g = grid_for((size_t)c->P * c->b, 256);
+    switch (c->ct) {
+        case AFR_F32: k_set_colors<AFR_F32><<<g, 256, 0, s>>>(rgb, c->foff, c->P, c->fcol); break;
+        case AFR_F16: k_set_colors<AFR_F16><<<g, 256, 0, s>>>(rgb, c->foff, c->P, c->fcol); break;
+        default: k_set_colors<AFR_BF16><<<g, 256, 0, s>>>(rgb, c->foff, c->P, c->fcol); break;
+    }
+    return cudaGetLastError();
+}
+
+int backward_blocks(int W, int H) {
+    return (int)(((W + kFilterBlock.x - 1) / kFilterBlock.x) * ((H + kFilterBlock.y - 1) / kFilterBlock.y));
+}
+
+}  // namespace afr

