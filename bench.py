@@ -138,7 +138,7 @@ def run_ours(args, rank, world):
 
     seed = rank
     t0 = time.time()
-    scene, batch = scenes.config_stream(WORKLOAD, seed)
+    scene, batch = scenes.config_stream(args.workload, seed)
     gen_s = time.time() - t0
     W, H, b = scene.width, scene.height, scene.spec.depth
     n = batch["pos"].shape[0]
@@ -172,7 +172,10 @@ def run_ours(args, rank, world):
 
     results = {}
     hbm_peak, peak_kind = _peaks()
-    for ct in (["f32", "f16", "bf16"] if not args.quick else ["f32"]):
+    forms = ["f32", "f16", "bf16"] if not (args.quick or args.profile) else ["f32"]
+    if args.color:
+        forms = [args.color]
+    for ct in forms:
         dtype = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[ct]
         rec = make(ct)
         pos, col, mo = to_device_batch(batch, dev, dtype)
@@ -186,7 +189,7 @@ def run_ours(args, rank, world):
             dist.barrier()
         torch.cuda.synchronize()
         clocks = None
-        if ct == "f32":
+        if ct == forms[0]:
             sampler = ClockSampler(local)
             sampler.start()
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -195,7 +198,7 @@ def run_ours(args, rank, world):
             step(rec, pos, col, mo, out, tiles, evs[k])
         end.record()
         torch.cuda.synchronize()
-        if ct == "f32":
+        if ct == forms[0]:
             clocks = sampler.stop()
         ms_total = start.elapsed_time(end)
         if dist:
@@ -209,18 +212,23 @@ def run_ours(args, rank, world):
         off, _, _ = (None, None, None)
         results[ct] = {"ms_per_step": ms_total / args.steps, "stage_ms": st_ms, "info": info, "clocks": clocks,
                        "csize": 16 if ct == "f32" else 8, "rec": rec, "out": out}
-        if ct != "f32":
+        if ct != forms[0]:
             rec.close()
             del pos, col, mo
             torch.cuda.empty_cache()
 
-    r32 = results["f32"]
+    r32 = results[forms[0]]
     rec = r32["rec"]
+    if args.profile:
+        print(json.dumps({"workload": args.workload, "color": forms[0], "ms_per_step": r32["ms_per_step"],
+                          "stage_ms": r32["stage_ms"], "info": r32["info"]}), flush=True)
+        rec.close()
+        return
     info = r32["info"]
     off, _, _ = rec.export_frame()
     pairs = pairs_of(off, W, H, 4)
     resident, frame = int(info["resident"]), int(info["frame"])
-    by = step_bytes(P, b, n, resident, frame, 16, rec.n_tiles)
+    by = step_bytes(P, b, n, resident, frame, r32["csize"], rec.n_tiles)
     step_ms = r32["ms_per_step"]
     total_bytes = sum(by.values())
     st = r32["stage_ms"]
@@ -408,6 +416,10 @@ def main():
     ap.add_argument("--quick", action="store_true", help="FP32 form only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default=WORKLOAD, help="workload key (workloads.scenes.CONFIGS)")
+    ap.add_argument("--color", default=None, choices=["f32", "f16", "bf16"], help="one colour form only")
+    ap.add_argument("--profile", action="store_true",
+                    help="time the step only (no end-to-end, adjoint or CPU legs); for profilers")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))

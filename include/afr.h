@@ -58,7 +58,8 @@ typedef enum { AFR_F32 = 0, AFR_F16 = 1, AFR_BF16 = 2 } AfrColorType;
 
 typedef struct {
     int32_t width, height;   /* image size in pixels, 1..16384 each */
-    int32_t depth;           /* b, queue depth per pixel, 1..32 (section 4 uses 4) */
+    int32_t depth;           /* b, queue depth per pixel, 1..32 (section 4 uses 4);
+                                width*height*depth must not exceed 2^28 */
     int32_t tile;            /* S, side of the density/statistics tiles, 1..256 (default 32) */
     int32_t radius;          /* R, filter footprint radius in bins, 0..8 (default 4) */
     int32_t color_type;      /* AfrColorType */

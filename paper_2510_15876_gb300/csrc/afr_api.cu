@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -33,8 +34,9 @@ cudaError_t dalloc(T **p, size_t n) {
 
 void free_all(AfrContext *c) {
     void *ptrs[] = {c->r_xy, c->r_mo, c->r_t, c->r_depth, c->r_seq, c->r_col, c->r_state, c->bin_of, c->idx,
+                    c->pack,
                     c->pcnt, c->poff, c->lbar, c->grad, c->pstat, c->sigma, c->amin2, c->tiles, c->fcnt,
-                    c->foff, c->fpos, c->fcol, c->scan_tmp, c->bgrad, c->bparam, c->dcount, c->derr};
+                    c->foff, c->fpos, c->fcol, c->fseq, c->scan_tmp, c->bgrad, c->bparam, c->dcount, c->derr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -99,7 +101,7 @@ AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
         g.color_type < AFR_F32 || g.color_type > AFR_BF16 || !(g.window > 0.f) || !std::isfinite(g.window) ||
         !(g.eps_grad > 0.f) || !(g.undersample_m >= 0.f))
         return AFR_ERR_INVALID_ARG;
-    if ((size_t)g.width * g.height * g.depth >= 0xFFFFFFFFull) return AFR_ERR_INVALID_ARG;
+    if ((size_t)g.width * g.height * g.depth > (1ull << 28)) return AFR_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();
@@ -146,6 +148,7 @@ AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
     AFR_ALLOC(c->foff, P + 1);
     AFR_ALLOC(c->fpos, 2 * N);
     if (e == cudaSuccess) e = cudaMalloc(&c->fcol, 2 * N * c->csize);
+    AFR_ALLOC(c->fseq, 2 * N);
     AFR_ALLOC(c->scan_tmp, c->scan_tmp_n);
     AFR_ALLOC(c->bgrad, 2 * P);
     AFR_ALLOC(c->bparam, (size_t)c->n_bblocks * 6);
@@ -187,21 +190,26 @@ AfrStatus afr_reset(AfrContext *c, afr_stream_t stream) {
     return AFR_OK;
 }
 
+static void free_batch(AfrContext *c) {
+    void *ptrs[] = {c->bin_of, c->idx, c->pack};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    c->bin_of = c->idx = nullptr;
+    c->pack = nullptr;
+    c->batch_cap = 0;
+}
+
 AfrStatus afr_reserve(AfrContext *c, uint32_t n) {
     if (!c) return AFR_ERR_INVALID_ARG;
     if (n <= c->batch_cap) return AFR_OK;
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(c, e, "afr_reserve");
-    if (c->bin_of) cudaFree(c->bin_of);
-    if (c->idx) cudaFree(c->idx);
-    c->bin_of = c->idx = nullptr;
-    c->batch_cap = 0;
+    free_batch(c);
     e = dalloc(&c->bin_of, n);
     if (e == cudaSuccess) e = dalloc(&c->idx, n);
+    if (e == cudaSuccess) e = cudaMalloc(&c->pack, (size_t)n * afr::packed_bytes(c->ct));
     if (e != cudaSuccess) {
-        if (c->bin_of) cudaFree(c->bin_of);
-        if (c->idx) cudaFree(c->idx);
-        c->bin_of = c->idx = nullptr;
+        free_batch(c);
         cudaGetLastError();
         return cuda_fail(c, e, "afr_reserve");
     }
@@ -404,6 +412,7 @@ AfrStatus afr_export_frame(AfrContext *c, uint32_t *off_host, float *rec_host, u
     if (n) {
         e = cudaMemcpy(pos.data(), c->fpos, n * 16, cudaMemcpyDeviceToHost);
         if (e == cudaSuccess) e = cudaMemcpy(col.data(), c->fcol, n * c->csize, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(seq_host, c->fseq, n * 4, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(c, e, "afr_export_frame");
     }
     for (size_t i = 0; i < n; ++i) {
@@ -412,9 +421,6 @@ AfrStatus afr_export_frame(AfrContext *c, uint32_t *off_host, float *rec_host, u
         o[1] = pos[i].y;
         o[2] = pos[i].z;
         widen_colors(c->ct, col.data(), i, o + 3);
-        uint32_t sq;
-        std::memcpy(&sq, &pos[i].w, 4);
-        seq_host[i] = sq;
     }
     return AFR_OK;
 }

@@ -55,8 +55,9 @@ struct AfrContext {
     uint32_t *r_state = nullptr;  // count | head << 16
 
     // ingest scratch
-    uint32_t *bin_of = nullptr;   // [batch_cap]
-    uint32_t *idx = nullptr;      // [batch_cap]
+    uint32_t *bin_of = nullptr;   // [batch_cap] pixel of each sample (kInvalid: rejected)
+    uint32_t *idx = nullptr;      // [batch_cap] batch indices sorted by pixel
+    void *pack = nullptr;         // [batch_cap] samples repacked into aligned records
     size_t batch_cap = 0;
     uint32_t *pcnt = nullptr;     // [P]
     uint32_t *poff = nullptr;     // [P+1]
@@ -72,8 +73,9 @@ struct AfrContext {
     // frame view
     uint32_t *fcnt = nullptr;     // [P]
     uint32_t *foff = nullptr;     // [P+1]
-    float4 *fpos = nullptr;       // [frame_cap] (x', y', a^2, seq bits)
-    void *fcol = nullptr;         // [frame_cap]
+    float4 *fpos = nullptr;       // [2*frame_cap] (x', y', a^2, bin column as int bits)
+    void *fcol = nullptr;         // [2*frame_cap]
+    uint32_t *fseq = nullptr;     // [2*frame_cap] sequence numbers
     size_t frame_cap = 0;
 
     // scan scratch
@@ -194,6 +196,7 @@ cudaError_t launch_backward(AfrContext *c, const float4 *grad_rgb, float *grad_c
                             cudaStream_t s);
 cudaError_t launch_set_frame_colors(AfrContext *c, const float *rgb, cudaStream_t s);
 int backward_blocks(int W, int H);
+size_t packed_bytes(int ct);
 cudaError_t launch_resident_count(AfrContext *c, cudaStream_t s);
 
 }  // namespace afr

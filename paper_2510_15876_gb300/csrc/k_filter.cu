@@ -102,47 +102,305 @@ __device__ __forceinline__ float shifted_exponent(const PixelFrame &f, float4 r)
     return fmaf(d2, f.ks, fmaf(r.z, f.kt, -f.m));
 }
 
-template <int CT, bool KAHAN>
-__global__ void __launch_bounds__(128) k_filter(int W, int H, int R, const float2 *__restrict__ sigma,
-                                                const uint32_t *__restrict__ amin2, const uint32_t *__restrict__ foff,
-                                                const float4 *__restrict__ fpos, const void *__restrict__ fcol,
-                                                float4 *__restrict__ out) {
-    using CS = ColorStore<CT>;
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= W || y >= H) return;
-    size_t p = (size_t)y * W + x;
-    PixelFrame f = pixel_frame(x, y, W, H, R, __ldg(sigma + p), amin2);
-    if (!f.any) {
-        out[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
+// Forward gather. One warp owns a 2x2 block of pixels. The bins of the union
+// of their four discs are enumerated first, with all lanes: each bin's record
+// range in the frame view and a 4-bit mask of the pixels whose disc holds it,
+// and the per-pixel exponent shifts. A prefix sum lays the bins' records out
+// in one index space; a per-warp map in shared memory lists, for each index,
+// the record and its mask. The gather then runs a flat loop: lane l takes
+// indices l, l+32, ... (two independent streams per iteration), so loads are
+// coalesced and every lane runs the same trip count whatever the bin
+// occupancy. A record outside a pixel's disc gets that pixel's exponent shift
+// -inf, i.e. weight 0. The arithmetic runs on pixel pairs (same row) with
+// paired FP32 instructions. Each lane accumulates the four pixels; the warp
+// reduces them at the end.
+constexpr int kMaxUnion = (2 * 8 + 2) * (2 * 8 + 2);   // union bins for R <= 8
+constexpr int kMapChunk = 512;                         // map entries per pass
+constexpr int kWarps = 8;
+
+typedef unsigned long long f2;   // two floats in one 64-bit register pair
+
+__device__ __forceinline__ f2 pk(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan_u(uint32_t v) {
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
     }
-    float S = 0.f, cS = 0.f, sr = 0.f, sg = 0.f, sb = 0.f;
-    for (int dy = -R; dy <= R; ++dy) {
-        int row = y + dy;
-        if (row < 0 || row >= H) continue;
-        int hw = half_width(R, dy);
-        int x0 = max(0, x - hw), x1 = min(W - 1, x + hw);
-        uint32_t e0 = __ldg(foff + (size_t)row * W + x0), e1 = __ldg(foff + (size_t)row * W + x1 + 1);
-        for (uint32_t e = e0; e < e1; ++e) {
-            float4 r = __ldg(fpos + e);
-            float3 c = CS::load(fcol, e);
-            float w = ex2(-shifted_exponent(f, r));
-            if (KAHAN) {
-                float yk = w - cS;
-                float tk = S + yk;
-                cS = (tk - S) - yk;
-                S = tk;
-            } else {
-                S += w;
-            }
-            sr = fmaf(w, c.x, sr);
-            sg = fmaf(w, c.y, sg);
-            sb = fmaf(w, c.z, sb);
+    return v;
+}
+
+// Reduces 16 per-lane values across the warp; afterwards lane l holds the
+// total of value ((l>>4)&1)*8 + ((l>>3)&1)*4 + ((l>>2)&1)*2 + ((l>>1)&1)
+// (transposed butterfly: 8 + 4 + 2 + 1 + 1 exchanges).
+__device__ __forceinline__ float warp_reduce16(float (&v)[16]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        bool hi = lane & 16;
+        float send = hi ? v[k] : v[k + 8];
+        float keep = hi ? v[k + 8] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        bool hi = lane & 8;
+        float send = hi ? v[k] : v[k + 4];
+        float keep = hi ? v[k + 4] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        bool hi = lane & 4;
+        float send = hi ? v[k] : v[k + 2];
+        float keep = hi ? v[k + 2] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {
+        bool hi = lane & 2;
+        float send = hi ? v[0] : v[1];
+        float keep = hi ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    return v[0];
+}
+
+// Pixel pair j (pixels (0, j) and (1, j)) constants and accumulators.
+struct PairConsts {
+    f2 cx;         // (cx0, cx1)
+    float cy[2];   // row centres
+    f2 nks[2], nkt[2];
+    float m[4];    // exponent shift per pixel
+};
+struct PairAcc {
+    f2 S[2], C[2], r[2], g[2], b[2];
+};
+
+template <bool KAHAN>
+__device__ __forceinline__ void accumulate(const PairConsts &pc, uint32_t mask, float4 rec, float3 c, PairAcc &A) {
+    const f2 dx = sub2(pk(rec.x, rec.x), pc.cx);
+    const f2 sx = mul2(dx, dx);
+    const f2 a2 = pk(rec.z, rec.z);
+    const f2 cr = pk(c.x, c.x), cg = pk(c.y, c.y), cb = pk(c.z, c.z);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float dy = rec.y - pc.cy[j];
+        const float sy = dy * dy;
+        const f2 d2 = add2(sx, pk(sy, sy));
+        // a record outside a pixel's disc gets exponent -inf: weight 0
+        const float m0 = (mask >> (2 * j)) & 1u ? pc.m[2 * j] : -INFINITY;
+        const float m1 = (mask >> (2 * j + 1)) & 1u ? pc.m[2 * j + 1] : -INFINITY;
+        const f2 e = fma2(d2, pc.nks[j], fma2(a2, pc.nkt[j], pk(m0, m1)));
+        float e0, e1;
+        upk(e, e0, e1);
+        const f2 w = pk(ex2(e0), ex2(e1));
+        if (KAHAN) {
+            const f2 y = sub2(w, A.C[j]);
+            const f2 t = add2(A.S[j], y);
+            A.C[j] = sub2(sub2(t, A.S[j]), y);
+            A.S[j] = t;
+        } else {
+            A.S[j] = add2(A.S[j], w);
         }
+        A.r[j] = fma2(w, cr, A.r[j]);
+        A.g[j] = fma2(w, cg, A.g[j]);
+        A.b[j] = fma2(w, cb, A.b[j]);
     }
-    float inv = 1.f / S;
-    out[p] = make_float4(sr * inv, sg * inv, sb * inv, S * ex2(-f.m));
+}
+
+template <int CT, bool KAHAN>
+__global__ void __launch_bounds__(256, 3) k_filter(int W, int H, int R, const float2 *__restrict__ sigma,
+                                                   const uint32_t *__restrict__ amin2,
+                                                   const uint32_t *__restrict__ foff, const float4 *__restrict__ fpos,
+                                                   const void *__restrict__ fcol, float4 *__restrict__ out) {
+    using CS = ColorStore<CT>;
+    __shared__ uint32_t map_sh[kWarps][kMapChunk];
+    __shared__ uint32_t bin_sh[kWarps][kMaxUnion][2];   // (first record, index offset) per union bin
+    __shared__ uint8_t bmask_sh[kWarps][kMaxUnion];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *map = map_sh[warp];
+    const int span = 2 * R + 2, nb = span * span;
+    for (int blk = warp; blk < 32; blk += kWarps) {
+        const int bx = blockIdx.x * 16 + (blk & 7) * 2, by = blockIdx.y * 8 + (blk >> 3) * 2;
+        if (bx >= W || by >= H) continue;   // warp-uniform
+        float ks_l = 0.f, kt_l = 0.f;
+        if (lane < 4) {
+            int x = bx + (lane & 1), y = by + (lane >> 1);
+            if (x < W && y < H) {
+                float2 sgm = __ldg(sigma + (size_t)y * W + x);
+                ks_l = kLog2e / (2.f * sgm.x * sgm.x);
+                kt_l = kLog2e / (2.f * sgm.y * sgm.y);
+            }
+        }
+        float ks[4], kt[4];
+        bool valid[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            ks[k] = __shfl_sync(0xffffffffu, ks_l, k);
+            kt[k] = __shfl_sync(0xffffffffu, kt_l, k);
+            valid[k] = bx + (k & 1) < W && by + (k >> 1) < H;
+        }
+        // union bins: (v, u) in [-R, R+1]^2 relative to the block; a bin enters
+        // if some valid pixel's disc holds it; its records, mask and the
+        // per-pixel exponent shift candidates
+        float mm[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
+        uint32_t carry = 0;
+        for (int t0 = 0; t0 < nb; t0 += 32) {
+            const int t = t0 + lane;
+            uint32_t cnt = 0, first = 0, mask = 0;
+            if (t < nb) {
+                const int v = t / span - R, u = t % span - R;
+                const int row = by + v, col = bx + u;
+                if (row >= 0 && row < H && col >= 0 && col < W) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        int du = u - (k & 1), dv = v - (k >> 1);
+                        if (valid[k] && du * du + dv * dv <= R * R) mask |= 1u << k;
+                    }
+                    if (mask) {
+                        const size_t q = (size_t)row * W + col;
+                        first = __ldg(foff + q);
+                        cnt = __ldg(foff + q + 1) - first;
+                        if (cnt) {
+                            const float a2 = __uint_as_float(__ldg(amin2 + q));
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                if (!((mask >> k) & 1u)) continue;
+                                float gx = bin_gap(u - (k & 1)), gy = bin_gap(v - (k >> 1));
+                                mm[k] = fminf(mm[k], fmaf(fmaf(gx, gx, gy * gy), ks[k], a2 * kt[k]));
+                            }
+                        }
+                    }
+                }
+            }
+            const uint32_t incl = warp_incl_scan_u(cnt);
+            if (t < nb) {
+                bin_sh[warp][t][0] = first;
+                bin_sh[warp][t][1] = carry + incl - cnt;
+                bmask_sh[warp][t] = (uint8_t)mask;
+            }
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        const uint32_t total = carry;
+        PairConsts pc;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            mm[k] = warp_min(mm[k]);
+            pc.m[k] = mm[k] < INFINITY ? mm[k] : 0.f;
+        }
+        pc.cx = pk((float)bx + 0.5f, (float)bx + 1.5f);
+        pc.cy[0] = (float)by + 0.5f;
+        pc.cy[1] = (float)by + 1.5f;
+        pc.nks[0] = pk(-ks[0], -ks[1]);
+        pc.nks[1] = pk(-ks[2], -ks[3]);
+        pc.nkt[0] = pk(-kt[0], -kt[1]);
+        pc.nkt[1] = pk(-kt[2], -kt[3]);
+        __syncwarp();
+        PairAcc A;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) A.S[j] = A.C[j] = A.r[j] = A.g[j] = A.b[j] = 0ull;
+        for (uint32_t w0 = 0; w0 < total; w0 += kMapChunk) {
+            const uint32_t w1 = min(total, w0 + (uint32_t)kMapChunk);
+            // map entries of this window: record index (28 bits) | pixel mask << 28
+            for (int t = lane; t < nb; t += 32) {
+                const uint32_t off = bin_sh[warp][t][1];
+                const uint32_t next = (t + 1 < nb) ? bin_sh[warp][t + 1][1] : total;
+                const uint32_t lo = max(off, w0), hi = min(next, w1);
+                if (lo >= hi) continue;
+                const uint32_t base = bin_sh[warp][t][0] - off, tag = (uint32_t)bmask_sh[warp][t] << 28;
+                for (uint32_t e = lo; e < hi; ++e) map[e - w0] = (base + e) | tag;
+            }
+            __syncwarp();
+            const uint32_t n = w1 - w0;
+            uint32_t j = lane;
+            for (; j + 32 < n; j += 64) {
+                const uint32_t ea = map[j], eb = map[j + 32];
+                const uint32_t ia = ea & 0x0FFFFFFFu, ib = eb & 0x0FFFFFFFu;
+                const float4 ra = __ldg(fpos + ia), rb = __ldg(fpos + ib);
+                const float3 ca = CS::load(fcol, ia), cbv = CS::load(fcol, ib);
+                accumulate<KAHAN>(pc, ea >> 28, ra, ca, A);
+                accumulate<KAHAN>(pc, eb >> 28, rb, cbv, A);
+            }
+            if (j < n) {
+                const uint32_t ea = map[j], ia = ea & 0x0FFFFFFFu;
+                accumulate<KAHAN>(pc, ea >> 28, __ldg(fpos + ia), CS::load(fcol, ia), A);
+            }
+            __syncwarp();
+        }
+        float vals[16];
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+            float a, b;
+            upk(KAHAN ? sub2(A.S[jj], A.C[jj]) : A.S[jj], a, b);
+            vals[2 * jj] = a;
+            vals[2 * jj + 1] = b;
+            upk(A.r[jj], a, b);
+            vals[4 + 2 * jj] = a;
+            vals[4 + 2 * jj + 1] = b;
+            upk(A.g[jj], a, b);
+            vals[8 + 2 * jj] = a;
+            vals[8 + 2 * jj + 1] = b;
+            upk(A.b[jj], a, b);
+            vals[12 + 2 * jj] = a;
+            vals[12 + 2 * jj + 1] = b;
+        }
+        const float tot = warp_reduce16(vals);
+        // value qq*4 + k (qq: S, r, g, b) of pixel k moves to lane k
+        float q[4];
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+            const int want = qq * 4 + (lane & 3);
+            const int src = ((want >> 3) & 1) * 16 + ((want >> 2) & 1) * 8 + ((want >> 1) & 1) * 4 + (want & 1) * 2;
+            q[qq] = __shfl_sync(0xffffffffu, tot, src);
+        }
+        if (lane < 4 && bx + (lane & 1) < W && by + (lane >> 1) < H) {
+            const int k = lane;
+            const float m = k == 0 ? pc.m[0] : k == 1 ? pc.m[1] : k == 2 ? pc.m[2] : pc.m[3];
+            float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q[0] > 0.f) {
+                const float inv = 1.f / q[0];
+                o = make_float4(q[1] * inv, q[2] * inv, q[3] * inv, q[0] * ex2(-m));
+            }
+            out[(size_t)(by + (k >> 1)) * W + bx + (k & 1)] = o;
+        }
+        __syncwarp();
+    }
 }
 
 // ---- adjoint -------------------------------------------------------------------
@@ -293,6 +551,7 @@ __global__ void k_set_colors(const float *__restrict__ rgb, const uint32_t *__re
 }
 
 const dim3 kFilterBlock(32, 4);
+const dim3 kQuadBlock(256);
 
 }  // namespace
 
@@ -304,18 +563,18 @@ cudaError_t launch_sigma(AfrContext *c, const AfrParams *prm, cudaStream_t s) {
 
 cudaError_t launch_filter(AfrContext *c, float t_now, float4 *out, cudaStream_t s) {
     (void)t_now;
-    dim3 grid((c->W + kFilterBlock.x - 1) / kFilterBlock.x, (c->H + kFilterBlock.y - 1) / kFilterBlock.y);
+    dim3 grid((c->W + 15) / 16, (c->H + 7) / 8);
     switch (c->ct) {
         case AFR_F32:
-            k_filter<AFR_F32, false><<<grid, kFilterBlock, 0, s>>>(c->W, c->H, c->R, c->sigma, c->amin2, c->foff,
+            k_filter<AFR_F32, false><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, c->sigma, c->amin2, c->foff,
                                                                    c->fpos, c->fcol, out);
             break;
         case AFR_F16:
-            k_filter<AFR_F16, true><<<grid, kFilterBlock, 0, s>>>(c->W, c->H, c->R, c->sigma, c->amin2, c->foff,
+            k_filter<AFR_F16, true><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, c->sigma, c->amin2, c->foff,
                                                                   c->fpos, c->fcol, out);
             break;
         default:
-            k_filter<AFR_BF16, true><<<grid, kFilterBlock, 0, s>>>(c->W, c->H, c->R, c->sigma, c->amin2, c->foff,
+            k_filter<AFR_BF16, true><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, c->sigma, c->amin2, c->foff,
                                                                    c->fpos, c->fcol, out);
             break;
     }

@@ -8,11 +8,10 @@
 //           aggregated) and keeps the smallest a^2 per bin (the filter's
 //           exponent shift).
 //  scan:    bin offsets.
-//  scatter: same slot walk, writes (x', y', a^2, seq) and the colour at the
-//           bin's next free record.
-//  order:   one warp per bin sorts its records by sequence number (a 32-lane
-//           bitonic network, looped merges up to 4096 records) so that the
-//           frame view, and every sum over it, is deterministic.
+//  scatter: same slot walk, writes (x', y', a^2, bin column) with the colour
+//           and the sequence number at the bin's next free record.
+//  order:   each record finds its rank by sequence number within its bin, so
+//           that the frame view, and every sum over it, is deterministic.
 #include "afr_internal.cuh"
 
 namespace afr {
@@ -35,6 +34,17 @@ __device__ __forceinline__ Moved move_sample(float2 xy, float2 m, float t, float
     return r;
 }
 
+// slot i -> (pixel, storage slot); b is a power of two in the common case
+__device__ __forceinline__ void split_slot(uint32_t i, int b, int bshift, uint32_t &p, int &s) {
+    if (bshift >= 0) {
+        p = i >> bshift;
+        s = (int)(i & (uint32_t)(b - 1));
+    } else {
+        p = i / (uint32_t)b;
+        s = (int)(i - p * (uint32_t)b);
+    }
+}
+
 __device__ __forceinline__ bool slot_live(uint32_t st, int s, int b) {
     int n = (int)(st & 0xFFFFu), h = (int)(st >> 16);
     int age = h - 1 - s;
@@ -42,14 +52,15 @@ __device__ __forceinline__ bool slot_live(uint32_t st, int s, int b) {
     return age < n;
 }
 
-__global__ void __launch_bounds__(256) k_count(size_t nslots, int b, int W, int H, float t_now,
+__global__ void __launch_bounds__(256) k_count(uint32_t nslots, int b, int bshift, int W, int H, float t_now,
                                                const uint32_t *__restrict__ state, const float2 *__restrict__ r_xy,
                                                const float2 *__restrict__ r_mo, const float *__restrict__ r_t,
                                                uint32_t *__restrict__ fcnt, uint32_t *__restrict__ amin2,
                                                unsigned long long *__restrict__ dcount) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nslots; i += (size_t)gridDim.x * blockDim.x) {
-        size_t p = i / b;
-        int s = (int)(i - p * b);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nslots; i += gridDim.x * blockDim.x) {
+        uint32_t p;
+        int s;
+        split_slot(i, b, bshift, p, s);
         if (!slot_live(__ldg(state + p), s, b)) continue;
         Moved mv = move_sample(__ldg(r_xy + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H);
         agg_count(dcount + CNT_DROPPED, !mv.ok);
@@ -63,80 +74,57 @@ __global__ void __launch_bounds__(256) k_count(size_t nslots, int b, int W, int 
 }
 
 template <int CT>
-__global__ void __launch_bounds__(256) k_scatter(size_t nslots, int b, int W, int H, float t_now,
+__global__ void __launch_bounds__(256) k_scatter(uint32_t nslots, int b, int bshift, int W, int H, float t_now,
                                                  const uint32_t *__restrict__ state, const float2 *__restrict__ r_xy,
                                                  const float2 *__restrict__ r_mo, const float *__restrict__ r_t,
                                                  const uint32_t *__restrict__ r_seq, const void *__restrict__ r_col,
                                                  const uint32_t *__restrict__ foff, uint32_t *__restrict__ fcur,
-                                                 float4 *__restrict__ fpos, void *__restrict__ fcol) {
+                                                 float4 *__restrict__ fpos, void *__restrict__ fcol,
+                                                 uint32_t *__restrict__ fseq) {
     using CS = ColorStore<CT>;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nslots; i += (size_t)gridDim.x * blockDim.x) {
-        size_t p = i / b;
-        int s = (int)(i - p * b);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nslots; i += gridDim.x * blockDim.x) {
+        uint32_t p;
+        int s;
+        split_slot(i, b, bshift, p, s);
         if (!slot_live(__ldg(state + p), s, b)) continue;
         Moved mv = move_sample(__ldg(r_xy + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H);
         if (!mv.ok) continue;
         uint32_t e = __ldg(foff + mv.bin) + agg_inc(fcur, mv.bin);
-        fpos[e] = make_float4(mv.xp, mv.yp, mv.a2, __uint_as_float(__ldg(r_seq + i)));
+        fpos[e] = make_float4(mv.xp, mv.yp, mv.a2, __int_as_float((int)floorf(mv.xp)));
         reinterpret_cast<typename CS::T *>(fcol)[e] = CS::raw(r_col, i);
+        fseq[e] = __ldg(r_seq + i);
     }
 }
 
-// 64-bit keys (seq << 32 | record) sorted ascending across a warp
-__device__ __forceinline__ unsigned long long warp_sort64(unsigned long long v) {
-    int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            unsigned long long o = __shfl_xor_sync(0xffffffffu, v, j);
-            bool up = ((lane & k) == 0), lower = ((lane & j) == 0);
-            v = (lower == up) ? (v < o ? v : o) : (v < o ? o : v);
-        }
-    }
-    return v;
-}
-
-// Orders the records of each bin by sequence number. Bins with up to 32
-// records sort in registers; larger bins (up to kSortedBinMax) are ranked by
-// counting smaller sequence numbers, lane-parallel; larger ones stay in
-// arrival order and are counted.
+// Orders the records of each bin by sequence number: one thread per record
+// counts the records of its bin with a smaller sequence number (sequence
+// numbers are unique) and moves its record there. Bins holding more than
+// kSortedBinMax records keep arrival order and are counted.
 template <int CT>
-__global__ void __launch_bounds__(256) k_order(int P, const uint32_t *__restrict__ foff,
+__global__ void __launch_bounds__(256) k_order(int W, const uint32_t *__restrict__ foff, uint32_t P,
                                                const float4 *__restrict__ src_pos, const void *__restrict__ src_col,
-                                               float4 *__restrict__ dst_pos, void *__restrict__ dst_col,
+                                               const uint32_t *__restrict__ src_seq, float4 *__restrict__ dst_pos,
+                                               void *__restrict__ dst_col, uint32_t *__restrict__ dst_seq,
                                                unsigned long long *__restrict__ dcount) {
     using CS = ColorStore<CT>;
     using T = typename CS::T;
-    const int lane = threadIdx.x & 31;
-    const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < P; q += warps) {
-        uint32_t beg = __ldg(foff + q), m = __ldg(foff + q + 1) - beg;
-        if (m == 0) continue;
-        if (m <= 32) {
-            unsigned long long key = ~0ull;
-            if (lane < (int)m) key = ((unsigned long long)__float_as_uint(src_pos[beg + lane].w) << 32) | (beg + lane);
-            key = warp_sort64(key);
-            if (lane < (int)m) {
-                uint32_t from = (uint32_t)key;
-                dst_pos[beg + lane] = src_pos[from];
-                reinterpret_cast<T *>(dst_col)[beg + lane] = CS::raw(src_col, from);
-            }
-        } else if (m <= (uint32_t)kSortedBinMax) {
-            for (uint32_t j = lane; j < m; j += 32) {
-                uint32_t sj = __float_as_uint(src_pos[beg + j].w);
-                uint32_t rank = 0;
-                for (uint32_t k = 0; k < m; ++k) rank += __float_as_uint(src_pos[beg + k].w) < sj;
-                dst_pos[beg + rank] = src_pos[beg + j];
-                reinterpret_cast<T *>(dst_col)[beg + rank] = CS::raw(src_col, beg + j);
-            }
-        } else {
-            for (uint32_t j = lane; j < m; j += 32) {
-                dst_pos[beg + j] = src_pos[beg + j];
-                reinterpret_cast<T *>(dst_col)[beg + j] = CS::raw(src_col, beg + j);
-            }
-            if (lane == 0) atomicAdd(dcount + CNT_UNSORTED, 1ull);
+    const uint32_t n = __ldg(foff + P);
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        float4 r = src_pos[e];
+        uint32_t bin = (uint32_t)(int)floorf(r.y) * (uint32_t)W + (uint32_t)__float_as_int(r.w);
+        uint32_t beg = __ldg(foff + bin), end = __ldg(foff + bin + 1);
+        uint32_t sq = src_seq[e];
+        uint32_t dst = e;
+        if (end - beg <= (uint32_t)kSortedBinMax) {
+            uint32_t rank = 0;
+            for (uint32_t k = beg; k < end; ++k) rank += __ldg(src_seq + k) < sq;
+            dst = beg + rank;
+        } else if (e == beg) {
+            atomicAdd(dcount + CNT_UNSORTED, 1ull);
         }
+        dst_pos[dst] = r;
+        reinterpret_cast<T *>(dst_col)[dst] = reinterpret_cast<const T *>(src_col)[e];
+        dst_seq[dst] = sq;
     }
 }
 
@@ -152,7 +140,9 @@ cudaError_t launch_reproject(AfrContext *c, float t_now, cudaStream_t s) {
     if ((e = cudaMemsetAsync(c->dcount + CNT_DROPPED, 0, sizeof(unsigned long long) * 2, s)) != cudaSuccess) return e;
     k_fill_u32<<<grid_for(c->P, 256), 256, 0, s>>>(c->amin2, c->P, 0x7f800000u);
     int g = grid_for(c->nslots, 256);
-    k_count<<<g, 256, 0, s>>>(c->nslots, c->b, c->W, c->H, t_now, c->r_state, c->r_xy, c->r_mo, c->r_t, c->fcnt,
+    const uint32_t ns = (uint32_t)c->nslots;
+    const int bshift = (c->b & (c->b - 1)) == 0 ? __builtin_ctz((unsigned)c->b) : -1;
+    k_count<<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, c->r_state, c->r_xy, c->r_mo, c->r_t, c->fcnt,
                               c->amin2, c->dcount);
     if ((e = scan_exclusive(c->fcnt, c->foff, c->P, c->scan_tmp, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->fcnt, 0, sizeof(uint32_t) * c->P, s)) != cudaSuccess) return e;
@@ -160,22 +150,26 @@ cudaError_t launch_reproject(AfrContext *c, float t_now, cudaStream_t s) {
     // writes them ordered into the first half
     float4 *tmp_pos = c->fpos + c->frame_cap;
     void *tmp_col = static_cast<char *>(c->fcol) + c->frame_cap * c->csize;
-    int go = grid_for((size_t)c->P * 32, 256);
+    uint32_t *tmp_seq = c->fseq + c->frame_cap;
+    int go = grid_for(c->nslots, 256);
     switch (c->ct) {
         case AFR_F32:
-            k_scatter<AFR_F32><<<g, 256, 0, s>>>(c->nslots, c->b, c->W, c->H, t_now, c->r_state, c->r_xy, c->r_mo, c->r_t,
-                                                 c->r_seq, c->r_col, c->foff, c->fcnt, tmp_pos, tmp_col);
-            k_order<AFR_F32><<<go, 256, 0, s>>>(c->P, c->foff, tmp_pos, tmp_col, c->fpos, c->fcol, c->dcount);
+            k_scatter<AFR_F32><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, c->r_state, c->r_xy, c->r_mo, c->r_t,
+                                                 c->r_seq, c->r_col, c->foff, c->fcnt, tmp_pos, tmp_col, tmp_seq);
+            k_order<AFR_F32><<<go, 256, 0, s>>>(c->W, c->foff, (uint32_t)c->P, tmp_pos, tmp_col, tmp_seq, c->fpos, c->fcol,
+                                                 c->fseq, c->dcount);
             break;
         case AFR_F16:
-            k_scatter<AFR_F16><<<g, 256, 0, s>>>(c->nslots, c->b, c->W, c->H, t_now, c->r_state, c->r_xy, c->r_mo, c->r_t,
-                                                 c->r_seq, c->r_col, c->foff, c->fcnt, tmp_pos, tmp_col);
-            k_order<AFR_F16><<<go, 256, 0, s>>>(c->P, c->foff, tmp_pos, tmp_col, c->fpos, c->fcol, c->dcount);
+            k_scatter<AFR_F16><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, c->r_state, c->r_xy, c->r_mo, c->r_t,
+                                                 c->r_seq, c->r_col, c->foff, c->fcnt, tmp_pos, tmp_col, tmp_seq);
+            k_order<AFR_F16><<<go, 256, 0, s>>>(c->W, c->foff, (uint32_t)c->P, tmp_pos, tmp_col, tmp_seq, c->fpos, c->fcol,
+                                                 c->fseq, c->dcount);
             break;
         default:
-            k_scatter<AFR_BF16><<<g, 256, 0, s>>>(c->nslots, c->b, c->W, c->H, t_now, c->r_state, c->r_xy, c->r_mo, c->r_t,
-                                                  c->r_seq, c->r_col, c->foff, c->fcnt, tmp_pos, tmp_col);
-            k_order<AFR_BF16><<<go, 256, 0, s>>>(c->P, c->foff, tmp_pos, tmp_col, c->fpos, c->fcol, c->dcount);
+            k_scatter<AFR_BF16><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, c->r_state, c->r_xy, c->r_mo, c->r_t,
+                                                  c->r_seq, c->r_col, c->foff, c->fcnt, tmp_pos, tmp_col, tmp_seq);
+            k_order<AFR_BF16><<<go, 256, 0, s>>>(c->W, c->foff, (uint32_t)c->P, tmp_pos, tmp_col, tmp_seq, c->fpos, c->fcol,
+                                                 c->fseq, c->dcount);
             break;
     }
     return cudaGetLastError();
