@@ -242,6 +242,38 @@ enum { AFR_RECON_KEEP_SIGMA = 1 };
 AFR_API AfrStatus afr_reconstruct_ex(AfrContext *ctx, float t_now, const AfrParams *params,
                              uint32_t flags, float *out_rgbw_dev, afr_stream_t stream);
 
+/* ---------------------------------------------------------------------
+ * Allocation-free variant (no counterpart in the paper).
+ * --------------------------------------------------------------------- */
+
+/* afr_reproject's move and binning applied directly to a caller-held batch,
+ * for callers that cannot allocate device memory when they need the step
+ * (a render thread with a fixed memory budget, a host whose frame callback
+ * forbids allocation): it needs no context and calls no allocator. Each
+ * sample of the batch that afr_insert_samples would accept is moved to
+ * t_now as afr_reproject moves it and binned at the pixel holding x'; the
+ * result is the frame view that afr_reproject builds from a context whose
+ * queues hold the whole batch.
+ *   batch        as for afr_insert_samples, colours in color_type
+ *   off_dev      width*height+1 uint32: record offset of each pixel's bin
+ *   rec_dev      n x float4 (x', y', a^2, bin column as int32 bits)
+ *   col_dev      n colours in color_type (16 or 8 bytes each)
+ *   seq_dev      n uint32: batch index of each record; within a bin records
+ *                are ordered by batch index
+ *   n_frame_dev  1 uint32: number of records written (may be NULL)
+ * The only scratch is one fixed device array of about 4 MB built into the
+ * library, held by every GPU that loads it until the process exits; it
+ * bounds width*height to 1,048,576 pixels, and n is bounded by 2^26. Larger
+ * sizes return AFR_ERR_INVALID_ARG, like null or misaligned pointers. The
+ * array's device address is looked up on the first call made with each
+ * device current (make that call before any stream capture). All calls
+ * share the array, so calls that overlap on the GPU race and must be
+ * serialised by the caller. Asynchronous on the stream. */
+AFR_API AfrStatus afr_reproject_batch_static(const AfrSampleBatch *batch, uint32_t n, int32_t width,
+                                             int32_t height, int32_t color_type, float t_now, uint32_t *off_dev,
+                                             float *rec_dev, void *col_dev, uint32_t *seq_dev,
+                                             uint32_t *n_frame_dev, afr_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

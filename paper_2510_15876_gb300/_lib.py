@@ -25,7 +25,7 @@ EXPORTED = [
     "afr_create", "afr_destroy", "afr_reset", "afr_reserve", "afr_insert_samples", "afr_estimate_gradients",
     "afr_reproject", "afr_reconstruct", "afr_reconstruct_ex", "afr_tile_feedback", "afr_reconstruct_backward",
     "afr_get_status", "afr_last_error", "afr_query", "afr_num_tiles", "afr_export_ring", "afr_export_frame",
-    "afr_export_map", "afr_import_map", "afr_set_frame_colors",
+    "afr_export_map", "afr_import_map", "afr_set_frame_colors", "afr_reproject_batch_static",
 ]
 
 
@@ -80,6 +80,8 @@ def _declare(L):
         "afr_export_map": (S, [c_p, c_i32, c_p]),
         "afr_import_map": (S, [c_p, c_i32, c_p]),
         "afr_set_frame_colors": (S, [c_p, c_p, c_p]),
+        "afr_reproject_batch_static": (S, [ctypes.POINTER(AfrSampleBatch), c_u32, c_i32, c_i32, c_i32, c_f32,
+                                           c_p, c_p, c_p, c_p, c_p, c_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
