@@ -242,6 +242,42 @@ enum { AFR_RECON_KEEP_SIGMA = 1 };
 AFR_API AfrStatus afr_reconstruct_ex(AfrContext *ctx, float t_now, const AfrParams *params,
                              uint32_t flags, float *out_rgbw_dev, afr_stream_t stream);
 
+/* Filter tuning of a context: footprint radius R (0..8; it changes results:
+ * the footprint is the integer disc of radius R) and the filter's CTA tile,
+ * (2*tile_bx) x (64/tile_bx) pixels with tile_bx in {2, 4, 8, 16} (default 8;
+ * it does not change results). */
+AFR_API AfrStatus afr_set_tuning(AfrContext *ctx, int32_t radius, int32_t tile_bx);
+
+/* ---------------------------------------------------------------------
+ * Batched form: many independent viewer streams (contexts) reconstructed in
+ * one persistent launch (no counterpart in the paper, which renders one
+ * stream). All contexts must share the colour type; at most 64.
+ * --------------------------------------------------------------------- */
+typedef struct AfrBatch AfrBatch;
+
+/* Freezes the set of contexts and their filter tile shapes (largest images
+ * are scheduled first). The contexts must outlive the batch. */
+AFR_API AfrStatus afr_batch_create(AfrContext *const *ctxs, int32_t n, AfrBatch **out);
+AFR_API void afr_batch_destroy(AfrBatch *batch);
+
+/* afr_reconstruct for every context in one launch: a persistent kernel takes
+ * width items (one band of a context's width map) and then filter items (one
+ * tile); a filter item waits, with a bounded spin of about 0.2 s, for its
+ * band's widths. If the wait runs out the tile is written as zeros and
+ * AFR_ERR_TIMEOUT is recorded in that context's status word (afr_get_status).
+ * outs_dev[i] receives context i's image (as afr_reconstruct). Each context
+ * needs afr_estimate_gradients and afr_reproject for t_now. The parameters
+ * and output pointers are staged in pinned host memory owned by the batch, so
+ * the call can be captured in a CUDA graph and replayed. */
+AFR_API AfrStatus afr_batch_reconstruct(AfrBatch *batch, float t_now, const AfrParams *params,
+                                        float *const *outs_dev, afr_stream_t stream);
+
+/* Fault injection for testing the bounded wait: until called again with -1,
+ * the width items of band `band` of context `ctx_index` (caller's index)
+ * leave their flag unset, so the filter items of that band run out their
+ * wait. */
+AFR_API AfrStatus afr_batch_inject_stall(AfrBatch *batch, int32_t ctx_index, int32_t band);
+
 /* ---------------------------------------------------------------------
  * Allocation-free variant (no counterpart in the paper).
  * --------------------------------------------------------------------- */

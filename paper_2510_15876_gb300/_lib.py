@@ -25,7 +25,8 @@ EXPORTED = [
     "afr_create", "afr_destroy", "afr_reset", "afr_reserve", "afr_insert_samples", "afr_estimate_gradients",
     "afr_reproject", "afr_reconstruct", "afr_reconstruct_ex", "afr_tile_feedback", "afr_reconstruct_backward",
     "afr_get_status", "afr_last_error", "afr_query", "afr_num_tiles", "afr_export_ring", "afr_export_frame",
-    "afr_export_map", "afr_import_map", "afr_set_frame_colors", "afr_reproject_batch_static",
+    "afr_export_map", "afr_import_map", "afr_set_frame_colors", "afr_reproject_batch_static", "afr_set_tuning",
+    "afr_batch_create", "afr_batch_destroy", "afr_batch_reconstruct", "afr_batch_inject_stall",
 ]
 
 
@@ -82,6 +83,11 @@ def _declare(L):
         "afr_set_frame_colors": (S, [c_p, c_p, c_p]),
         "afr_reproject_batch_static": (S, [ctypes.POINTER(AfrSampleBatch), c_u32, c_i32, c_i32, c_i32, c_f32,
                                            c_p, c_p, c_p, c_p, c_p, c_p]),
+        "afr_set_tuning": (S, [c_p, c_i32, c_i32]),
+        "afr_batch_create": (S, [ctypes.POINTER(c_p), c_i32, ctypes.POINTER(c_p)]),
+        "afr_batch_destroy": (None, [c_p]),
+        "afr_batch_reconstruct": (S, [c_p, c_f32, ctypes.POINTER(AfrParams), ctypes.POINTER(c_p), c_p]),
+        "afr_batch_inject_stall": (S, [c_p, c_i32, c_i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

@@ -195,3 +195,50 @@ def to_device_batch(batch: dict, device, color_dtype=torch.float32):
     col = torch.from_numpy(np.ascontiguousarray(batch["color"], np.float32)).to(device).to(color_dtype)
     mo = torch.from_numpy(np.ascontiguousarray(batch["motion"], np.float32)).to(device)
     return pos.contiguous(), col.contiguous(), mo.contiguous()
+
+
+class BatchReconstructor:
+    """Many Reconstructors of one colour type reconstructed in one persistent
+    launch (afr_batch_reconstruct). The contexts must outlive the batch; their
+    filter tile shapes are frozen at creation."""
+
+    def __init__(self, recs: list[Reconstructor]):
+        self.lib = L.load()
+        self.recs = list(recs)
+        arr = (ctypes.c_void_p * len(recs))(*[r.h.value for r in recs])
+        h = ctypes.c_void_p()
+        st = self.lib.afr_batch_create(arr, len(recs), ctypes.byref(h))
+        if st != L.AFR_OK:
+            raise L.AfrError(st, "afr_batch_create failed")
+        self.h = h
+        self.outs = [torch.empty((r.H, r.W, 4), dtype=torch.float32, device=r.device) for r in recs]
+        self._ptrs = (ctypes.c_void_p * len(recs))(*[o.data_ptr() for o in self.outs])
+
+    def run(self, t_now: float = 1.0, params=None, stream=None) -> list[torch.Tensor]:
+        prm = _params(params)
+        st = self.lib.afr_batch_reconstruct(self.h, t_now, ctypes.byref(prm), self._ptrs, _stream(stream))
+        if st != L.AFR_OK:
+            raise L.AfrError(st, "afr_batch_reconstruct failed")
+        return self.outs
+
+    def inject_stall(self, ctx_index: int, band: int):
+        st = self.lib.afr_batch_inject_stall(self.h, ctx_index, band)
+        if st != L.AFR_OK:
+            raise L.AfrError(st, "afr_batch_inject_stall failed")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.afr_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def set_tuning(rec: Reconstructor, radius: int, tile_bx: int):
+    rec._check(rec.lib.afr_set_tuning(rec.h, radius, tile_bx))
+    rec.R = radius
+    rec.tile_bx = tile_bx

@@ -90,6 +90,20 @@ cudaError_t launch_resident_count(AfrContext *c, cudaStream_t s) {
 }
 }  // namespace afr
 
+struct AfrBatch {
+    std::vector<AfrContext *> ctxs;  // queue order (largest first)
+    std::vector<int> user_index;     // caller's index of each queue position
+    std::vector<int> tile_bx;        // tile shape each context had at creation
+    afr::BatchCtx *h_ctx = nullptr;  // pinned staging of the device records
+    afr::BatchCtx *d_ctx = nullptr;
+    uint32_t *d_queue = nullptr;
+    uint32_t *d_flags = nullptr;
+    uint32_t nflags = 0, totalA = 0, totalB = 0;
+    uint32_t skip = 0xFFFFFFFFu;
+    long long wait_cycles = 400000000LL;   // about 0.2 s at the maximum SM clock
+    int ct = 0, grid = 0;
+};
+
 extern "C" {
 
 AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
@@ -474,6 +488,156 @@ AfrStatus afr_set_frame_colors(AfrContext *c, const float *rgb_dev, afr_stream_t
     cudaError_t e = afr::launch_set_frame_colors(c, rgb_dev, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(c, e, "afr_set_frame_colors");
     c->recon_valid = false;
+    return AFR_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+AfrStatus afr_set_tuning(AfrContext *c, int32_t radius, int32_t tile_bx) {
+    if (!c) return AFR_ERR_INVALID_ARG;
+    if (radius < 0 || radius > 8 || !(tile_bx == 2 || tile_bx == 4 || tile_bx == 8 || tile_bx == 16))
+        return fail(c, AFR_ERR_INVALID_ARG, "afr_set_tuning: radius 0..8, tile_bx 2, 4, 8 or 16");
+    c->R = radius;
+    c->cfg.radius = radius;
+    c->tile_bx = tile_bx;
+    c->recon_valid = false;
+    return AFR_OK;
+}
+
+void afr_batch_destroy(AfrBatch *b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    if (b->h_ctx) cudaFreeHost(b->h_ctx);
+    if (b->d_ctx) cudaFree(b->d_ctx);
+    if (b->d_queue) cudaFree(b->d_queue);
+    if (b->d_flags) cudaFree(b->d_flags);
+    delete b;
+}
+
+AfrStatus afr_batch_create(AfrContext *const *ctxs, int32_t n, AfrBatch **out) {
+    if (!ctxs || !out || n < 1 || n > 64) return AFR_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i)
+        if (!ctxs[i] || ctxs[i]->ct != ctxs[0]->ct) return AFR_ERR_INVALID_ARG;
+    AfrBatch *b = new (std::nothrow) AfrBatch();
+    if (!b) return AFR_ERR_OOM;
+    b->ct = ctxs[0]->ct;
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return ctxs[a]->P > ctxs[c]->P; });
+    for (int i : order) {
+        b->ctxs.push_back(ctxs[i]);
+        b->user_index.push_back(i);
+        b->tile_bx.push_back(ctxs[i]->tile_bx);
+    }
+    cudaError_t e = cudaMallocHost(&b->h_ctx, sizeof(afr::BatchCtx) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_ctx, sizeof(afr::BatchCtx) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, sizeof(uint32_t));
+    uint32_t a = 0, f = 0;
+    for (int q = 0; q < n; ++q) {
+        AfrContext *c = b->ctxs[q];
+        const int tw = 2 * b->tile_bx[q], th = 2 * (32 / b->tile_bx[q]);
+        const uint32_t bands = (uint32_t)((c->H + th - 1) / th), tx = (uint32_t)((c->W + tw - 1) / tw);
+        b->h_ctx[q].band0 = a;
+        b->h_ctx[q].a0 = a;
+        b->h_ctx[q].b0 = f;
+        a += bands;
+        f += bands * tx;
+    }
+    b->nflags = b->totalA = a;
+    b->totalB = f;
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_flags, sizeof(uint32_t) * (a ? a : 1));
+    int dev = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        afr_batch_destroy(b);
+        return e == cudaErrorMemoryAllocation ? AFR_ERR_OOM : AFR_ERR_CUDA;
+    }
+    b->grid = 3 * sms;
+    *out = b;
+    return AFR_OK;
+}
+
+AfrStatus afr_batch_inject_stall(AfrBatch *b, int32_t ctx_index, int32_t band) {
+    if (!b) return AFR_ERR_INVALID_ARG;
+    if (ctx_index < 0 || band < 0) {
+        b->skip = 0xFFFFFFFFu;
+        return AFR_OK;
+    }
+    for (size_t q = 0; q < b->ctxs.size(); ++q) {
+        if (b->user_index[q] != ctx_index) continue;
+        const uint32_t next = q + 1 < b->ctxs.size() ? b->h_ctx[q + 1].band0 : b->nflags;
+        if (b->h_ctx[q].band0 + (uint32_t)band >= next) return AFR_ERR_INVALID_ARG;
+        b->skip = b->h_ctx[q].band0 + (uint32_t)band;
+        return AFR_OK;
+    }
+    return AFR_ERR_INVALID_ARG;
+}
+
+AfrStatus afr_batch_reconstruct(AfrBatch *b, float t_now, const AfrParams *params, float *const *outs_dev,
+                                afr_stream_t stream) {
+    if (!b || !params || !outs_dev) return AFR_ERR_INVALID_ARG;
+    if (!params_ok(params)) return AFR_ERR_INVALID_ARG;
+    const int n = (int)b->ctxs.size();
+    std::vector<afr::BatchCtx> rec(b->h_ctx, b->h_ctx + n);
+    for (int q = 0; q < n; ++q) {
+        AfrContext *c = b->ctxs[q];
+        float *o = outs_dev[b->user_index[q]];
+        if (!o || !aligned(o, 16)) return fail(c, AFR_ERR_INVALID_ARG, "afr_batch_reconstruct: bad output pointer");
+        if (!c->frame_valid || c->frame_t != t_now || !c->grads_valid || c->grads_t != t_now)
+            return fail(c, AFR_ERR_BAD_STATE, "afr_batch_reconstruct: estimate gradients and reproject first");
+        if (c->tile_bx != b->tile_bx[q])
+            return fail(c, AFR_ERR_BAD_STATE, "afr_batch_reconstruct: tile shape changed since afr_batch_create");
+        afr::BatchCtx &x = rec[q];
+        x.W = c->W;
+        x.H = c->H;
+        x.R = c->R;
+        x.S = c->S;
+        x.ntx = c->ntx;
+        x.tbx = c->tile_bx;
+        x.th = 2 * (32 / c->tile_bx);
+        x.ntiles_x = (c->W + 2 * c->tile_bx - 1) / (2 * c->tile_bx);
+        x.window = c->cfg.window;
+        x.eps = c->cfg.eps_grad;
+        x.prm = *params;
+        x.grad = c->grad;
+        x.tiles = c->tiles;
+        x.sigma = c->sigma;
+        x.amin2 = c->amin2;
+        x.foff = c->foff;
+        x.fpos = c->fpos;
+        x.fcol = c->fcol;
+        x.out = reinterpret_cast<float4 *>(o);
+        x.derr = c->derr;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // the pinned staging buffer may still feed an earlier copy on the stream:
+    // rewrite it only when the records change, after the stream drains (a
+    // stream being captured has nothing in flight)
+    if (std::memcmp(rec.data(), b->h_ctx, sizeof(afr::BatchCtx) * n) != 0) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+        if (ce == cudaSuccess && cap == cudaStreamCaptureStatusNone) ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) return cuda_fail(b->ctxs[0], ce, "afr_batch_reconstruct");
+        std::memcpy(b->h_ctx, rec.data(), sizeof(afr::BatchCtx) * n);
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_ctx, b->h_ctx, sizeof(afr::BatchCtx) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queue, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_flags, 0, sizeof(uint32_t) * (b->nflags ? b->nflags : 1), s);
+    if (e == cudaSuccess)
+        e = afr::launch_batch(b->ct, b->d_ctx, n, b->totalA, b->totalA + b->totalB, b->d_queue, b->d_flags, b->skip,
+                              b->wait_cycles, b->grid, s);
+    if (e != cudaSuccess) return cuda_fail(b->ctxs[0], e, "afr_batch_reconstruct");
+    for (AfrContext *c : b->ctxs) {
+        c->recon_valid = true;
+        c->recon_t = t_now;
+        c->recon_params = *params;
+        c->sigma_imported = false;
+    }
     return AFR_OK;
 }
 

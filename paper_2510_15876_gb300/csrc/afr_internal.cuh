@@ -35,6 +35,24 @@ struct TilePartial {
     double sgx, sgy, sgt;  // gradient sums over non-empty pixels
 };
 
+// Per-context record of a batched launch (device memory).
+struct BatchCtx {
+    int W, H, R, S, ntx, tbx, th, ntiles_x;
+    float window, eps;
+    AfrParams prm;
+    const float4 *grad;
+    const TilePartial *tiles;
+    float2 *sigma;
+    const uint32_t *amin2;
+    const uint32_t *foff;
+    const float4 *fpos;
+    const void *fcol;
+    float4 *out;
+    uint32_t *derr;
+    uint32_t band0;     // first band flag of this context
+    uint32_t a0, b0;    // first width item, first filter item (filter items counted from 0)
+};
+
 }  // namespace afr
 
 struct AfrContext {
@@ -100,6 +118,7 @@ struct AfrContext {
     float recon_t = 0.f;
     AfrParams recon_params{};
     bool sigma_imported = false;
+    int tile_bx = 8;              // filter CTA tile: (2*tile_bx) x (64/tile_bx) pixels
     std::string err;
 };
 
@@ -196,6 +215,8 @@ cudaError_t launch_backward(AfrContext *c, const float4 *grad_rgb, float *grad_c
                             cudaStream_t s);
 cudaError_t launch_set_frame_colors(AfrContext *c, const float *rgb, cudaStream_t s);
 int backward_blocks(int W, int H);
+cudaError_t launch_batch(int ct, const BatchCtx *cs, int nctx, uint32_t totalA, uint32_t total, uint32_t *queue,
+                         uint32_t *flags, uint32_t skip_flag, long long wait_cycles, int grid, cudaStream_t s);
 size_t packed_bytes(int ct);
 cudaError_t launch_resident_count(AfrContext *c, cudaStream_t s);
 

@@ -244,26 +244,29 @@ __device__ __forceinline__ void accumulate(const PairConsts &pc, uint32_t mask, 
     }
 }
 
-template <int CT, bool KAHAN>
-__global__ void __launch_bounds__(256, 3) k_filter(int W, int H, int R, const float2 *__restrict__ sigma,
-                                                   const uint32_t *__restrict__ amin2,
-                                                   const uint32_t *__restrict__ foff, const float4 *__restrict__ fpos,
-                                                   const void *__restrict__ fcol, float4 *__restrict__ out) {
+// One 2x2 pixel block (top-left pixel bx, by) by one warp; smem holds the
+// warp's map and bin tables.
+struct QuadSmem {
+    uint32_t map[kMapChunk];
+    uint32_t bin[kMaxUnion][2];   // (first record, index offset) per union bin
+    uint8_t bmask[kMaxUnion];
+};
+
+template <int CT, bool KAHAN, bool COHERENT = false>
+__device__ __forceinline__ void filter_block(int W, int H, int R, int bx, int by, const float2 *__restrict__ sigma,
+                                             const uint32_t *__restrict__ amin2, const uint32_t *__restrict__ foff,
+                                             const float4 *__restrict__ fpos, const void *__restrict__ fcol,
+                                             float4 *__restrict__ out, QuadSmem &sm) {
     using CS = ColorStore<CT>;
-    __shared__ uint32_t map_sh[kWarps][kMapChunk];
-    __shared__ uint32_t bin_sh[kWarps][kMaxUnion][2];   // (first record, index offset) per union bin
-    __shared__ uint8_t bmask_sh[kWarps][kMaxUnion];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *map = map_sh[warp];
+    const int lane = threadIdx.x & 31;
+    uint32_t *map = sm.map;
     const int span = 2 * R + 2, nb = span * span;
-    for (int blk = warp; blk < 32; blk += kWarps) {
-        const int bx = blockIdx.x * 16 + (blk & 7) * 2, by = blockIdx.y * 8 + (blk >> 3) * 2;
-        if (bx >= W || by >= H) continue;   // warp-uniform
         float ks_l = 0.f, kt_l = 0.f;
         if (lane < 4) {
             int x = bx + (lane & 1), y = by + (lane >> 1);
             if (x < W && y < H) {
-                float2 sgm = __ldg(sigma + (size_t)y * W + x);
+                // widths written earlier in the same launch are read through L2
+                float2 sgm = COHERENT ? __ldcg(sigma + (size_t)y * W + x) : __ldg(sigma + (size_t)y * W + x);
                 ks_l = kLog2e / (2.f * sgm.x * sgm.x);
                 kt_l = kLog2e / (2.f * sgm.y * sgm.y);
             }
@@ -311,9 +314,9 @@ __global__ void __launch_bounds__(256, 3) k_filter(int W, int H, int R, const fl
             }
             const uint32_t incl = warp_incl_scan_u(cnt);
             if (t < nb) {
-                bin_sh[warp][t][0] = first;
-                bin_sh[warp][t][1] = carry + incl - cnt;
-                bmask_sh[warp][t] = (uint8_t)mask;
+                sm.bin[t][0] = first;
+                sm.bin[t][1] = carry + incl - cnt;
+                sm.bmask[t] = (uint8_t)mask;
             }
             carry += __shfl_sync(0xffffffffu, incl, 31);
         }
@@ -339,11 +342,11 @@ __global__ void __launch_bounds__(256, 3) k_filter(int W, int H, int R, const fl
             const uint32_t w1 = min(total, w0 + (uint32_t)kMapChunk);
             // map entries of this window: record index (28 bits) | pixel mask << 28
             for (int t = lane; t < nb; t += 32) {
-                const uint32_t off = bin_sh[warp][t][1];
-                const uint32_t next = (t + 1 < nb) ? bin_sh[warp][t + 1][1] : total;
+                const uint32_t off = sm.bin[t][1];
+                const uint32_t next = (t + 1 < nb) ? sm.bin[t + 1][1] : total;
                 const uint32_t lo = max(off, w0), hi = min(next, w1);
                 if (lo >= hi) continue;
-                const uint32_t base = bin_sh[warp][t][0] - off, tag = (uint32_t)bmask_sh[warp][t] << 28;
+                const uint32_t base = sm.bin[t][0] - off, tag = (uint32_t)sm.bmask[t] << 28;
                 for (uint32_t e = lo; e < hi; ++e) map[e - w0] = (base + e) | tag;
             }
             __syncwarp();
@@ -399,7 +402,103 @@ __global__ void __launch_bounds__(256, 3) k_filter(int W, int H, int R, const fl
             }
             out[(size_t)(by + (k >> 1)) * W + bx + (k & 1)] = o;
         }
-        __syncwarp();
+    __syncwarp();
+}
+
+// Tile of (2 * tbx) x (2 * 32 / tbx) pixels per CTA: 32 blocks of 2x2, four
+// per warp.
+template <int CT, bool KAHAN>
+__global__ void __launch_bounds__(256, 3) k_filter(int W, int H, int R, int tbx, const float2 *__restrict__ sigma,
+                                                   const uint32_t *__restrict__ amin2,
+                                                   const uint32_t *__restrict__ foff, const float4 *__restrict__ fpos,
+                                                   const void *__restrict__ fcol, float4 *__restrict__ out) {
+    __shared__ QuadSmem smem[kWarps];
+    const int warp = threadIdx.x >> 5;
+    const int tby = 32 / tbx;
+    for (int blk = warp; blk < 32; blk += kWarps) {
+        const int bx = blockIdx.x * 2 * tbx + (blk % tbx) * 2, by = blockIdx.y * 2 * tby + (blk / tbx) * 2;
+        if (bx >= W || by >= H) continue;   // warp-uniform
+        filter_block<CT, KAHAN>(W, H, R, bx, by, sigma, amin2, foff, fpos, fcol, out, smem[warp]);
+    }
+}
+
+// ---- batched persistent launch ----------------------------------------------
+// One launch reconstructs many contexts. A work queue (one atomic counter)
+// hands out, first, width items (one band of th rows of one context: the
+// width map of the band, then a release flag) and then filter items (one
+// tw x th tile). A filter item waits for its band's flag with a bounded spin
+// (clock-limited, with back-off); if the limit passes it records ERR_TIMEOUT
+// in its context's status word, writes zeros for the tile and moves on, so
+// the launch always ends. Items are taken in queue order, so a filter item
+// only ever waits for a width item already taken by a running CTA.
+template <int CT, bool KAHAN>
+__global__ void __launch_bounds__(256, 3) k_batch(const BatchCtx *__restrict__ cs, int nctx, uint32_t totalA,
+                                                  uint32_t total, uint32_t *queue, uint32_t *flags,
+                                                  uint32_t skip_flag, long long wait_cycles) {
+    __shared__ QuadSmem smem[kWarps];
+    __shared__ uint32_t item_sh;
+    __shared__ int ok_sh;
+    const int warp = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) item_sh = atomicAdd(queue, 1u);
+        __syncthreads();
+        const uint32_t item = item_sh;
+        if (item >= total) break;
+        if (item < totalA) {
+            int c = 0;
+            while (c + 1 < nctx && cs[c + 1].a0 <= item) ++c;
+            const BatchCtx &x = cs[c];
+            const int k = (int)(item - x.a0);
+            const int y0 = k * x.th, y1 = min(x.H, y0 + x.th);
+            for (int p = y0 * x.W + threadIdx.x; p < y1 * x.W; p += blockDim.x) {
+                const int px = p % x.W, py = p / x.W;
+                Widths w = widths(__ldg(x.grad + p), tile_volume(px, py, x.W, x.H, x.S, x.ntx, x.window, x.tiles),
+                                  x.eps, x.prm);
+                x.sigma[p] = make_float2(w.ss, w.st);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0 && x.band0 + (uint32_t)k != skip_flag) {
+                __threadfence();
+                atomicExch(flags + x.band0 + k, 1u);
+            }
+        } else {
+            const uint32_t j = item - totalA;
+            int c = 0;
+            while (c + 1 < nctx && cs[c + 1].b0 <= j) ++c;
+            const BatchCtx &x = cs[c];
+            const uint32_t local = j - x.b0;
+            const int k = (int)(local / (uint32_t)x.ntiles_x), i = (int)(local % (uint32_t)x.ntiles_x);
+            if (threadIdx.x == 0) {
+                const long long t0 = clock64();
+                int ok = 1;
+                while (atomicAdd(flags + x.band0 + k, 0u) == 0u) {
+                    if (clock64() - t0 > wait_cycles) {
+                        ok = 0;
+                        atomicOr(x.derr, ERR_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+                __threadfence();
+                ok_sh = ok;
+            }
+            __syncthreads();
+            const int tbx = x.tbx, tby = 32 / tbx;
+            if (ok_sh) {
+                for (int blk = warp; blk < 32; blk += kWarps) {
+                    const int bx = i * 2 * tbx + (blk % tbx) * 2, by = k * 2 * tby + (blk / tbx) * 2;
+                    if (bx >= x.W || by >= x.H) continue;
+                    filter_block<CT, KAHAN, true>(x.W, x.H, x.R, bx, by, x.sigma, x.amin2, x.foff, x.fpos, x.fcol,
+                                                  x.out, smem[warp]);
+                }
+            } else {
+                for (int t = threadIdx.x; t < 4 * 32; t += blockDim.x) {
+                    const int px = i * 2 * tbx + t % (2 * tbx), py = k * 2 * tby + t / (2 * tbx);
+                    if (px < x.W && py < x.H) x.out[(size_t)py * x.W + px] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -563,18 +662,19 @@ cudaError_t launch_sigma(AfrContext *c, const AfrParams *prm, cudaStream_t s) {
 
 cudaError_t launch_filter(AfrContext *c, float t_now, float4 *out, cudaStream_t s) {
     (void)t_now;
-    dim3 grid((c->W + 15) / 16, (c->H + 7) / 8);
+    const int tbx = c->tile_bx, tw = 2 * tbx, th = 2 * (32 / tbx);
+    dim3 grid((c->W + tw - 1) / tw, (c->H + th - 1) / th);
     switch (c->ct) {
         case AFR_F32:
-            k_filter<AFR_F32, false><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, c->sigma, c->amin2, c->foff,
+            k_filter<AFR_F32, false><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, tbx, c->sigma, c->amin2, c->foff,
                                                                    c->fpos, c->fcol, out);
             break;
         case AFR_F16:
-            k_filter<AFR_F16, true><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, c->sigma, c->amin2, c->foff,
+            k_filter<AFR_F16, true><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, tbx, c->sigma, c->amin2, c->foff,
                                                                   c->fpos, c->fcol, out);
             break;
         default:
-            k_filter<AFR_BF16, true><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, c->sigma, c->amin2, c->foff,
+            k_filter<AFR_BF16, true><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, tbx, c->sigma, c->amin2, c->foff,
                                                                    c->fpos, c->fcol, out);
             break;
     }
@@ -610,6 +710,25 @@ cudaError_t launch_set_frame_colors(AfrContext *c, const float *rgb, cudaStream_
         case AFR_F32: k_set_colors<AFR_F32><<<g, 256, 0, s>>>(rgb, c->foff, c->P, c->fcol); break;
         case AFR_F16: k_set_colors<AFR_F16><<<g, 256, 0, s>>>(rgb, c->foff, c->P, c->fcol); break;
         default: k_set_colors<AFR_BF16><<<g, 256, 0, s>>>(rgb, c->foff, c->P, c->fcol); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch(int ct, const BatchCtx *cs, int nctx, uint32_t totalA, uint32_t total, uint32_t *queue,
+                         uint32_t *flags, uint32_t skip_flag, long long wait_cycles, int grid, cudaStream_t s) {
+    switch (ct) {
+        case AFR_F32:
+            k_batch<AFR_F32, false><<<grid, kQuadBlock, 0, s>>>(cs, nctx, totalA, total, queue, flags, skip_flag,
+                                                                wait_cycles);
+            break;
+        case AFR_F16:
+            k_batch<AFR_F16, true><<<grid, kQuadBlock, 0, s>>>(cs, nctx, totalA, total, queue, flags, skip_flag,
+                                                               wait_cycles);
+            break;
+        default:
+            k_batch<AFR_BF16, true><<<grid, kQuadBlock, 0, s>>>(cs, nctx, totalA, total, queue, flags, skip_flag,
+                                                                wait_cycles);
+            break;
     }
     return cudaGetLastError();
 }

@@ -1,0 +1,143 @@
+"""Batched form: several viewer streams of different sizes and depths in one
+persistent launch (afr_batch_reconstruct), tuned by the autotuner, captured
+in a CUDA graph, and the bounded wait of its width/filter hand-off."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from workloads.scenes import SceneSpec, make_scene, sample_stream
+
+pytestmark = pytest.mark.gpu
+
+from paper_2510_15876_gb300 import _lib as L  # noqa: E402
+
+STREAMS = [(96, 64, 4, 10), (130, 70, 8, 24), (64, 48, 16, 16), (200, 120, 8, 40)]   # (W, H, depth, discs)
+T_NOW = 1.0
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_15876_gb300.build import build
+    build()
+    return torch.device("cuda:0")
+
+
+def _make(dev, ct="f16"):
+    from paper_2510_15876_gb300.api import Reconstructor, to_device_batch
+    recs, batches = [], []
+    for i, (W, H, b, k) in enumerate(STREAMS):
+        sc = make_scene(SceneSpec(f"batch_test{i}", W, H, b, k, (4.0, 16.0), 24.0, 8), i)
+        batch = sample_stream(sc, W * H * b, i)
+        rec = Reconstructor(W, H, b, color_type=ct, device=dev)
+        rec.insert(*to_device_batch(batch, dev, rec.color_dtype))
+        rec.estimate_gradients(T_NOW)
+        rec.reproject(T_NOW)
+        recs.append(rec)
+        batches.append(batch)
+    return recs, batches
+
+
+def test_batch_matches_single_stream_launches(dev):
+    from paper_2510_15876_gb300 import autotune
+    from paper_2510_15876_gb300.api import BatchReconstructor
+    recs, _ = _make(dev)
+    tuned = [autotune.tune(r) for r in recs]
+    assert all(r in autotune.RADII and t in autotune.TILES for r, t in tuned)
+    singles = [r.reconstruct(T_NOW).clone() for r in recs]
+    B = BatchReconstructor(recs)
+    outs = B.run(T_NOW)
+    torch.cuda.synchronize()
+    for a, b in zip(singles, outs):
+        assert torch.equal(a, b)
+    assert all(r.status() == L.AFR_OK for r in recs)
+    B.close()
+
+
+def test_batch_against_oracle_at_chosen_radius(dev):
+    from paper_2510_15876_gb300 import autotune
+    from paper_2510_15876_gb300.api import BatchReconstructor
+    recs, batches = _make(dev)
+    radii = [autotune.tune(r)[0] for r in recs]
+    B = BatchReconstructor(recs)
+    outs = [o.clone().cpu().numpy().reshape(-1, 4).astype(np.float64) for o in B.run(T_NOW)]
+    for (W, H, b, _), batch, R, got in zip(STREAMS, batches, radii, outs):
+        col16 = torch.from_numpy(batch["color"]).half().float().numpy()   # the stored colours
+        ring = oracle.Ring(W, H, b)
+        ring.insert(batch["pos"], col16, batch["motion"])
+        ref = oracle.reconstruct(ring, R=R)["image"]
+        hole = ref[:, 3] == 0
+        assert np.all(got[hole, :3] == 0)
+        err = np.abs(got[~hole, :3] - ref[~hole, :3]) / np.maximum(np.abs(ref[~hole, :3]), 1e-3)
+        assert np.quantile(err, 0.999) < 1e-4 and err.max() < 1e-2, (R, np.quantile(err, 0.999), err.max())
+    B.close()
+
+
+def test_batch_graph_replay(dev):
+    from paper_2510_15876_gb300 import autotune
+    from paper_2510_15876_gb300.api import BatchReconstructor
+    recs, _ = _make(dev)
+    for r in recs:
+        autotune.tune(r)
+    B = BatchReconstructor(recs)
+
+    def step():
+        for r in recs:
+            r.estimate_gradients(T_NOW)
+            r.reproject(T_NOW)
+        B.run(T_NOW)
+
+    step()
+    torch.cuda.synchronize()
+    ref = [o.clone() for o in B.outs]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    for o in B.outs:
+        o.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(ref, B.outs):
+        assert torch.equal(a, b)
+    assert all(r.status() == L.AFR_OK for r in recs)
+    B.close()
+
+
+def test_batch_bounded_wait_reports_timeout(dev):
+    """A width band whose flag is never set: its filter items give up after
+    their bounded wait, the context reports AFR_ERR_TIMEOUT, the others are
+    untouched, and the next launch works again."""
+    from paper_2510_15876_gb300.api import BatchReconstructor
+    recs, _ = _make(dev, ct="f32")
+    B = BatchReconstructor(recs)
+    ref = [o.clone() for o in B.run(T_NOW)]
+    torch.cuda.synchronize()
+    B.inject_stall(1, 0)
+    t0 = time.time()
+    outs = B.run(T_NOW)
+    torch.cuda.synchronize()
+    dt = time.time() - t0
+    assert recs[1].status() == L.AFR_ERR_TIMEOUT
+    assert all(recs[i].status() == L.AFR_OK for i in (0, 2, 3))
+    th = 8   # band height of the default filter tile (16 x 8)
+    assert torch.all(outs[1][:th] == 0)
+    assert torch.equal(outs[1][th:], ref[1][th:])
+    for i in (0, 2, 3):
+        assert torch.equal(outs[i], ref[i])
+    assert dt < 10.0
+    B.inject_stall(-1, -1)
+    outs = B.run(T_NOW)
+    torch.cuda.synchronize()
+    assert all(r.status() == L.AFR_OK for r in recs)
+    for a, b in zip(ref, outs):
+        assert torch.equal(a, b)
+    B.close()
