@@ -8,6 +8,12 @@ ingest the batch (section 4), estimate gradients (4.1), reproject to t_now
 6.1). The batch (1.3 GB) and the buffers are far larger than L2, so no flush
 is needed between steps.
 
+The same run also times the FP16- and BF16-stored forms of that step, the
+forward+backward of the 512x512x8 differentiation workload, the batched form
+(48 streams, one persistent launch in a CUDA graph, against 48 sequential
+single-stream launches), the step end to end through the Python API with the
+batch in pinned host memory, and the CPU oracle on a band of the workload.
+
 Prints one JSON line. --impl reference times the CPU oracle instead (a band
 of the same workload per step, scaled to whole images).
 """
@@ -30,8 +36,10 @@ import numpy as np  # noqa: E402
 WORKLOAD = "c3_1920x1080x16"
 METRIC = "1080p reconstructions/s (16-deep buffer)"
 T_NOW = 1.0
-# kernels launched per call (memsets excluded), as the launch sequences in csrc/ issue them
-LAUNCHES = {"ingest": 6, "gradients": 3, "reproject": 7, "reconstruct": 2, "feedback": 1}
+# kernels launched per call of the step (memsets and copies excluded), as the
+# launch sequences in csrc/ issue them
+LAUNCHES = {"ingest": 6, "gradients": 2, "reproject": 7, "reconstruct": 2, "feedback": 1}
+STAGES = ["ingest", "gradients", "reproject", "reconstruct", "feedback"]
 
 
 def _peaks():
@@ -41,6 +49,17 @@ def _peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """Maximum of a per-rank value over all ranks (the whole job is as slow as
+    its slowest replica)."""
+    if dist is None or not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 class ClockSampler:
@@ -57,10 +76,11 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            time.sleep(0.3)
         except Exception:
             self.proc = None
 
@@ -71,33 +91,33 @@ class ClockSampler:
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.25)
+        time.sleep(0.15)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm = [float(r[0]) for r in self.rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        ok = [r for r in self.rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
+        sm = [float(r[0]) for r in ok]
+        mx = [float(r[1]) for r in ok if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in self.rows if len(r) >= 8 for k in range(4)
-                          if r[4 + k].lower() == "active"})
+        reasons = sorted({names[k] for r in ok for k in range(4) if r[4 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(sm)}
 
 
 # ------------------------------------------------------------------------------ workload bytes
-def step_bytes(P, b, n_batch, resident, frame, csize, ntiles):
-    """Algorithmic HBM bytes of one step (each operand read or written once).
-    csize: stored colour bytes (16 FP32 / 8 FP16). Sample fields: x,y,mx,my
-    (16 B), t (4), depth (4), seq (4), colour."""
-    ingest = n_batch * (16 + csize + 8) + resident * (16 + 4 + 4 + 4 + csize) + P * 4
-    grads = resident * (4 + csize + 4) + P * (4 + 16 + 16 + 4) + ntiles * 64
-    reproj = resident * (16 + 4 + 4 + csize) + frame * (16 + csize) + P * 8
-    recon = frame * (16 + csize) + P * (16 + 8 + 4 + 4 + 16)
+def stage_bytes(P, n_batch, resident, frame, csize, ntiles):
+    """Algorithmic HBM bytes of each stage (each operand read or written once).
+    csize: stored colour bytes (16 FP32 / 8 16-bit). A buffered sample is
+    x, y, mx, my (16 B), t (4), depth (4), seq (4) and its colour; a frame
+    record is x', y', a^2, bin column (16 B), its colour and seq (4)."""
+    ingest = n_batch * (16 + csize + 8) + resident * (16 + 4 + 4 + 4 + csize) + P * 8
+    grads = resident * (4 + 4 + csize) + P * (4 + 4 + 16 + 4 + 16) + ntiles * 64
+    reproj = resident * (16 + 4 + 4 + csize) + frame * (16 + csize + 4) + P * 12
+    recon = frame * (16 + csize) + P * (16 + 8 + 4 + 8 + 16)
     feedback = ntiles * (64 + 32)
-    return {"ingest": ingest, "gradients": grads, "reproject": reproj, "reconstruct": recon,
-            "feedback": feedback}
+    return {"ingest": ingest, "gradients": grads, "reproject": reproj, "reconstruct": recon, "feedback": feedback}
 
 
 def pairs_of(off, W, H, R):
@@ -106,7 +126,6 @@ def pairs_of(off, W, H, R):
     tot = 0
     for dy in range(-R, R + 1):
         hw = int(np.floor(np.sqrt(R * R - dy * dy) + 1e-9))
-        rows = np.zeros((H, W), np.int64)
         src = np.roll(cnt, -dy, axis=0)
         if dy > 0:
             src[H - dy:] = 0
@@ -114,10 +133,7 @@ def pairs_of(off, W, H, R):
             src[:-dy] = 0
         cs = np.concatenate([np.zeros((H, 1), np.int64), np.cumsum(src, axis=1)], axis=1)
         x = np.arange(W)
-        x0 = np.maximum(0, x - hw)
-        x1 = np.minimum(W - 1, x + hw)
-        rows = cs[:, x1 + 1] - cs[:, x0]
-        tot += int(rows.sum())
+        tot += int((cs[:, np.minimum(W - 1, x + hw) + 1] - cs[:, np.maximum(0, x - hw)]).sum())
     return tot
 
 
@@ -143,12 +159,6 @@ def run_ours(args, rank, world):
     W, H, b = scene.width, scene.height, scene.spec.depth
     n = batch["pos"].shape[0]
     P = W * H
-    stream = torch.cuda.current_stream()
-
-    def make(ct):
-        r = Reconstructor(W, H, b, color_type=ct, device=dev)
-        r.reserve(n)
-        return r
 
     def step(r, pos, col, mo, out, tiles, ev=None):
         if ev is not None:
@@ -175,9 +185,11 @@ def run_ours(args, rank, world):
     forms = ["f32", "f16", "bf16"] if not (args.quick or args.profile) else ["f32"]
     if args.color:
         forms = [args.color]
+    keep = None
     for ct in forms:
         dtype = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[ct]
-        rec = make(ct)
+        rec = Reconstructor(W, H, b, color_type=ct, device=dev)
+        rec.reserve(n)
         pos, col, mo = to_device_batch(batch, dev, dtype)
         out = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
         tiles = torch.empty((rec.n_tiles, 8), dtype=torch.float32, device=dev)
@@ -188,9 +200,8 @@ def run_ours(args, rank, world):
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        clocks = None
-        if ct == forms[0]:
-            sampler = ClockSampler(local)
+        sampler = ClockSampler(local) if ct == forms[0] else None
+        if sampler:
             sampler.start()
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         start.record()
@@ -198,68 +209,59 @@ def run_ours(args, rank, world):
             step(rec, pos, col, mo, out, tiles, evs[k])
         end.record()
         torch.cuda.synchronize()
-        if ct == forms[0]:
-            clocks = sampler.stop()
-        ms_total = start.elapsed_time(end)
+        clocks = sampler.stop() if sampler else None
         if dist:
-            tt = torch.tensor([ms_total], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms_total = float(tt.item())
             dist.barrier()
-        stages = ["ingest", "gradients", "reproject", "reconstruct", "feedback"]
-        st_ms = {s: sum(e[i].elapsed_time(e[i + 1]) for e in evs) / args.steps for i, s in enumerate(stages)}
-        info = rec.query()
-        off, _, _ = (None, None, None)
-        results[ct] = {"ms_per_step": ms_total / args.steps, "stage_ms": st_ms, "info": info, "clocks": clocks,
-                       "csize": 16 if ct == "f32" else 8, "rec": rec, "out": out}
-        if ct != forms[0]:
+        ms_total = max_over_ranks(start.elapsed_time(end), dist, dev)
+        st_ms = {s: sum(e[i].elapsed_time(e[i + 1]) for e in evs) / args.steps for i, s in enumerate(STAGES)}
+        results[ct] = {"ms_per_step": ms_total / args.steps, "stage_ms": st_ms, "info": rec.query(),
+                       "clocks": clocks, "csize": 16 if ct == "f32" else 8}
+        if ct == forms[0]:
+            keep = (rec, pos, col, mo, out, tiles)
+        else:
             rec.close()
             del pos, col, mo
             torch.cuda.empty_cache()
 
-    r32 = results[forms[0]]
-    rec = r32["rec"]
+    r0 = results[forms[0]]
+    rec = keep[0]
     if args.profile:
-        print(json.dumps({"workload": args.workload, "color": forms[0], "ms_per_step": r32["ms_per_step"],
-                          "stage_ms": r32["stage_ms"], "info": r32["info"]}), flush=True)
+        if rank == 0:
+            print(json.dumps({"workload": args.workload, "color": forms[0], "ms_per_step": r0["ms_per_step"],
+                              "stage_ms": r0["stage_ms"], "info": r0["info"]}), flush=True)
         rec.close()
         return
-    info = r32["info"]
+
+    info = r0["info"]
     off, _, _ = rec.export_frame()
     pairs = pairs_of(off, W, H, 4)
     resident, frame = int(info["resident"]), int(info["frame"])
-    by = step_bytes(P, b, n, resident, frame, r32["csize"], rec.n_tiles)
-    step_ms = r32["ms_per_step"]
+    by = stage_bytes(P, n, resident, frame, r0["csize"], rec.n_tiles)
+    step_ms = r0["ms_per_step"]
+    st = r0["stage_ms"]
     total_bytes = sum(by.values())
-    st = r32["stage_ms"]
-    # dominant stage and its roofline
-    dom = max(st, key=st.get)
-    if dom == "reconstruct":
-        flops = pairs * 16.0
-        peak_tf = 152 * 128 * 2 * 2.07e9 / 1e12
-        ach = flops / (st[dom] * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "k_filter (+k_sigma)", "achieved": round(ach, 2), "peak": round(peak_tf, 1),
-                "unit": "TFLOP/s", "frac": round(ach / peak_tf, 4), "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz",
-                "work": f"{pairs} pairs x 16 FLOP"}
-    else:
-        ach = by[dom] / (st[dom] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(ach / hbm_peak, 4), "traffic": None, "peak_source": peak_kind}
+    flops = pairs * 16.0
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    ach = flops / (st["reconstruct"] * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": "k_filter (with k_sigma, 0.7% of the stage)", "achieved": round(ach, 2),
+            "peak": round(fp32_peak, 1), "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
+            "traffic": args.filter_traffic,
+            "peak_source": "FP32 issue peak: 152 SMs x 128 lanes x 2 FLOP (FMA) x 2.07 GHz",
+            "work": f"{pairs} sample-pixel pairs x 16 FLOP"}
+    stage_hbm = {s: round(by[s] / (st[s] * 1e-3) / 1e9 / hbm_peak, 4) for s in STAGES}
 
-    # end to end through the public API with host buffers
+    # end to end through the public API, batch in pinned host memory
     import torch as _t
+    _, pos, col, mo, out, tiles = keep
     hp = {k: _t.from_numpy(np.ascontiguousarray(batch[k], np.float32)).pin_memory() for k in ("pos", "color", "motion")}
-    dpos, dcol, dmo = (_t.empty_like(hp[k], device=dev) for k in ("pos", "color", "motion"))
     host_img = _t.empty((H, W, 4), dtype=_t.float32).pin_memory()
-    tiles = _t.empty((rec.n_tiles, 8), dtype=_t.float32, device=dev)
 
     def e2e_step():
-        dpos.copy_(hp["pos"], non_blocking=True)
-        dcol.copy_(hp["color"], non_blocking=True)
-        dmo.copy_(hp["motion"], non_blocking=True)
-        step(rec, dpos, dcol, dmo, r32["out"], tiles)
-        host_img.copy_(r32["out"], non_blocking=True)
+        pos.copy_(hp["pos"], non_blocking=True)
+        col.copy_(hp["color"], non_blocking=True)
+        mo.copy_(hp["motion"], non_blocking=True)
+        step(rec, pos, col, mo, out, tiles)
+        host_img.copy_(out, non_blocking=True)
 
     for _ in range(max(1, args.warmup // 2)):
         e2e_step()
@@ -271,26 +273,30 @@ def run_ours(args, rank, world):
         e2e_step()
     e2.record()
     _t.cuda.synchronize()
-    e2e_ms = s2.elapsed_time(e2) / k2
+    e2e_ms = max_over_ranks(s2.elapsed_time(e2) / k2, dist, dev)
     h2d = sum(hp[k].numel() * 4 for k in hp)
     d2h = host_img.numel() * 4
+    rec.close()
+    del keep, pos, col, mo, hp
+    _t.cuda.empty_cache()
 
-    # fwd+bwd on the 512x512x8 differentiation workload
     fb = run_fwd_bwd(args, dev)
+    batched = None if (args.quick or args.no_batched) else run_batched(args, dev)
 
     value = world * 1000.0 / step_ms
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "reconstructions/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD} (1920x1080 image, 16-deep buffer, {n} samples per batch, 256 moving "
-                               f"discs, 10% occlusion-edge pixels, seed {seed})",
+        "config": {"workload": f"{args.workload} (1920x1080 image, 16-deep buffer, {n} samples per batch, 256 "
+                               f"moving discs, 10% occlusion-edge pixels, seed {seed})",
                    "global_batch": n * world, "l2": "inputs larger than L2 (1.3 GB batch), no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "mpixel_per_s": round(P * value / 1e6, 1),
         "samples_filtered_per_s": round(frame * value, 0),
         "pairs_per_step": pairs,
         "hbm_frac_step": round(total_bytes / (step_ms * 1e-3) / 1e9 / hbm_peak, 4),
+        "hbm_frac_stage": stage_hbm,
         "step_bytes": total_bytes,
         "stage_ms": {k: round(v, 4) for k, v in st.items()},
         "roofline": roof,
@@ -298,15 +304,15 @@ def run_ours(args, rank, world):
                                  "stage_ms": {k: round(v, 4) for k, v in results[ct]["stage_ms"].items()}}
                             for ct in results},
         "fwd_bwd": fb,
+        "batched": batched,
         "e2e": {"value": round(world * 1000.0 / e2e_ms, 3), "unit": "reconstructions/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * sum(LAUNCHES.values()),
-        "clocks": r32["clocks"],
+        "clocks": r0["clocks"],
         "resident": resident, "frame": frame, "generation_s": round(gen_s, 1),
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, batch, args.cpu_seconds)
-    rec.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -315,14 +321,15 @@ def run_ours(args, rank, world):
 
 
 def run_fwd_bwd(args, dev):
+    """afr_reconstruct + afr_reconstruct_backward (colours and parameters) on
+    the 512x512x8 differentiation workload."""
     import torch
     from paper_2510_15876_gb300.api import Reconstructor, to_device_batch
     from workloads import scenes
     sc, batch = scenes.config_stream("c4_512x512x8", 0)
     W, H, b = sc.width, sc.height, sc.spec.depth
     rec = Reconstructor(W, H, b, device=dev)
-    pos, col, mo = to_device_batch(batch, dev)
-    rec.insert(pos, col, mo)
+    rec.insert(*to_device_batch(batch, dev))
     rec.estimate_gradients(T_NOW)
     rec.reproject(T_NOW)
     n_frame = rec.query()["frame"]
@@ -342,8 +349,94 @@ def run_fwd_bwd(args, dev):
     e.record()
     torch.cuda.synchronize()
     rec.close()
-    return {"config": "c4_512x512x8 (512x512, 8-deep, 2,097,152 samples)", "ms_per_step": round(s.elapsed_time(e) / k, 4),
-            "what": "afr_reconstruct + afr_reconstruct_backward (colours and 6 parameters)"}
+    return {"config": "c4_512x512x8 (512x512, 8-deep, 2,097,152 samples, 32 moving discs)",
+            "ms_per_step": round(s.elapsed_time(e) / k, 4),
+            "what": "afr_reconstruct + afr_reconstruct_backward (frame colours and 6 parameters)"}
+
+
+def run_batched(args, dev, n_streams: int = 48):
+    """48 viewer streams (seeds 0-47; sizes, depths and disc counts drawn per
+    stream), FP16 colours, each tuned by the autotuner. The batched step is
+    every stream's gradients and reprojection plus one persistent
+    afr_batch_reconstruct launch, captured in a CUDA graph; the baseline is the
+    same work as 48 sequential single-stream launch sequences."""
+    import torch
+    from paper_2510_15876_gb300 import autotune
+    from paper_2510_15876_gb300.api import BatchReconstructor, Reconstructor
+    from workloads import scenes
+    from workloads.gpu_scenes import sample_stream_gpu
+    t0 = time.time()
+    recs = []
+    for i, sp in enumerate(scenes.batched_specs(n_streams)):
+        sc = scenes.make_scene(sp, i)
+        pos, col, mo = sample_stream_gpu(sc, sp.n_samples, i, dev)
+        rec = Reconstructor(sp.width, sp.height, sp.depth, color_type="f16", device=dev)
+        rec.insert(pos, col.half().contiguous(), mo)
+        del pos, col, mo
+        rec.estimate_gradients(T_NOW)
+        rec.reproject(T_NOW)
+        recs.append(rec)
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+    tuned = [autotune.tune(r, T_NOW) for r in recs]
+    B = BatchReconstructor(recs)
+    outs = [torch.empty((r.H, r.W, 4), dtype=torch.float32, device=dev) for r in recs]
+
+    def batched_step():
+        for r in recs:
+            r.estimate_gradients(T_NOW)
+            r.reproject(T_NOW)
+        B.run(T_NOW)
+
+    def sequential_step():
+        for r, o in zip(recs, outs):
+            r.estimate_gradients(T_NOW)
+            r.reproject(T_NOW)
+            r.reconstruct(T_NOW, out=o)
+
+    def timed(fn, k):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(k):
+            fn()
+        e.record()
+        torch.cuda.synchronize()
+        return s.elapsed_time(e) / k
+
+    k = max(3, args.steps // 4)
+    seq_ms = timed(sequential_step, k)
+    batch_ms = timed(batched_step, k)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        batched_step()
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        batched_step()
+    graph_ms = timed(g.replay, k)
+    status = [r.status() for r in recs]
+    pixels = sum(r.W * r.H for r in recs)
+    res = {
+        "streams": n_streams, "pixels": pixels, "samples": sum(r.W * r.H * r.b for r in recs),
+        "graph_ms_per_step": round(graph_ms, 3), "batched_ms_per_step": round(batch_ms, 3),
+        "sequential_ms_per_step": round(seq_ms, 3),
+        "mpixel_per_s_graph": round(pixels / graph_ms / 1e3, 1),
+        "mpixel_per_s_sequential": round(pixels / seq_ms / 1e3, 1),
+        "radius_counts": {str(rr): sum(1 for t in tuned if t[0] == rr) for rr in autotune.RADII},
+        "tile_counts": {str(tt): sum(1 for t in tuned if t[1] == tt) for tt in autotune.TILES},
+        "status_ok": all(s_ == 0 for s_ in status), "generation_s": round(gen_s, 1),
+        "what": "per stream afr_estimate_gradients + afr_reproject, then one afr_batch_reconstruct (CUDA graph) "
+                "vs per stream afr_reconstruct launches",
+    }
+    B.close()
+    for r in recs:
+        r.close()
+    torch.cuda.empty_cache()
+    return res
 
 
 # ------------------------------------------------------------------------------ oracle arm
@@ -375,8 +468,9 @@ def cpu_baseline(scene, batch, budget_s):
         k += 1
     per_image = secs / k * (H / band)
     return {"value": round(1.0 / per_image, 6), "unit": "reconstructions/s", "cores": 1, "kind": "oracle",
-            "sample": f"{k} runs of the whole oracle path on a {scene.width}x{band} band of the workload "
-                      f"(its samples only), scaled by {H}/{band} rows"}
+            "sample": f"{k} runs of the whole oracle path (ingest, gradients, tile statistics, reprojection, "
+                      f"widths, filter) on a {scene.width}x{band} band of the workload (its samples only), "
+                      f"scaled by {H}/{band} rows"}
 
 
 def run_reference(args, rank, world):
@@ -413,16 +507,19 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--quick", action="store_true", help="FP32 form only")
+    ap.add_argument("--quick", action="store_true", help="FP32 form only, no batched form")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default=WORKLOAD, help="workload key (workloads.scenes.CONFIGS)")
     ap.add_argument("--color", default=None, choices=["f32", "f16", "bf16"], help="one colour form only")
     ap.add_argument("--profile", action="store_true",
-                    help="time the step only (no end-to-end, adjoint or CPU legs); for profilers")
+                    help="time the step only (no end-to-end, adjoint, batched or CPU legs); for profilers")
+    ap.add_argument("--filter-traffic", type=float, default=None,
+                    help="DRAM bytes per k_filter launch from an ncu capture of the current build")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:
