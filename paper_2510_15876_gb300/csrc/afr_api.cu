@@ -35,7 +35,7 @@ cudaError_t dalloc(T **p, size_t n) {
 void free_all(AfrContext *c) {
     void *ptrs[] = {c->r_xy, c->r_mo, c->r_t, c->r_depth, c->r_seq, c->r_col, c->r_state, c->bin_of, c->idx,
                     c->pack,
-                    c->pcnt, c->poff, c->lbar, c->grad, c->pstat, c->sigma, c->amin2, c->tiles, c->fcnt,
+                    c->pcnt, c->poff, c->lbar, c->grad, c->pstat, c->sigma, c->fconst, c->amin2, c->tiles, c->fcnt,
                     c->foff, c->fpos, c->fcol, c->fseq, c->scan_tmp, c->bgrad, c->bparam, c->dcount, c->derr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -156,6 +156,7 @@ AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
     AFR_ALLOC(c->grad, P);
     AFR_ALLOC(c->pstat, P);
     AFR_ALLOC(c->sigma, P);
+    AFR_ALLOC(c->fconst, P);
     AFR_ALLOC(c->amin2, P);
     AFR_ALLOC(c->tiles, (size_t)c->ntiles);
     AFR_ALLOC(c->fcnt, P);
@@ -292,7 +293,7 @@ AfrStatus afr_reconstruct_ex(AfrContext *c, float t_now, const AfrParams *params
         return fail(c, AFR_ERR_BAD_STATE, "afr_reconstruct: call afr_estimate_gradients for this t_now first");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
-    if (!keep) e = afr::launch_sigma(c, params, s);
+    e = afr::launch_sigma(c, params, keep, s);
     if (e == cudaSuccess) e = afr::launch_filter(c, t_now, reinterpret_cast<float4 *>(out_rgbw_dev), s);
     if (e != cudaSuccess) return cuda_fail(c, e, "afr_reconstruct");
     c->recon_valid = true;
@@ -607,6 +608,7 @@ AfrStatus afr_batch_reconstruct(AfrBatch *b, float t_now, const AfrParams *param
         x.grad = c->grad;
         x.tiles = c->tiles;
         x.sigma = c->sigma;
+        x.fconst = c->fconst;
         x.amin2 = c->amin2;
         x.foff = c->foff;
         x.fpos = c->fpos;

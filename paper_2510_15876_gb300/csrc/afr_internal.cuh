@@ -43,6 +43,7 @@ struct BatchCtx {
     const float4 *grad;
     const TilePartial *tiles;
     float2 *sigma;
+    float4 *fconst;
     const uint32_t *amin2;
     const uint32_t *foff;
     const float4 *fpos;
@@ -85,6 +86,7 @@ struct AfrContext {
     float4 *grad = nullptr;       // [P] (Gx, Gy, Gt, Lbar)
     float4 *pstat = nullptr;      // [P] (sum w, mean L, M2, Gt)
     float2 *sigma = nullptr;      // [P] (sigma_s, sigma_t)
+    float4 *fconst = nullptr;     // [P] gather constants (-ks, -kt, exponent shift m, 0) of each pixel
     uint32_t *amin2 = nullptr;    // [P] float bits of min a^2 per frame bin
     afr::TilePartial *tiles = nullptr;  // [ntiles]
 
@@ -208,7 +210,7 @@ cudaError_t launch_ingest(AfrContext *c, const AfrSampleBatch *batch, uint32_t n
                           cudaStream_t s);
 cudaError_t launch_gradients(AfrContext *c, float t_now, cudaStream_t s);
 cudaError_t launch_reproject(AfrContext *c, float t_now, cudaStream_t s);
-cudaError_t launch_sigma(AfrContext *c, const AfrParams *prm, cudaStream_t s);
+cudaError_t launch_sigma(AfrContext *c, const AfrParams *prm, bool keep, cudaStream_t s);
 cudaError_t launch_filter(AfrContext *c, float t_now, float4 *out, cudaStream_t s);
 cudaError_t launch_feedback(AfrContext *c, AfrTileStats *out, cudaStream_t s);
 cudaError_t launch_backward(AfrContext *c, const float4 *grad_rgb, float *grad_col, float *grad_prm,

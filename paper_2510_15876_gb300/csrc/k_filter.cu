@@ -41,17 +41,6 @@ __device__ __forceinline__ float tile_volume(int x, int y, int W, int H, int S, 
     return n > 0.f ? A * window / n : A * window;
 }
 
-__global__ void __launch_bounds__(256) k_sigma(int W, int H, int S, int ntx, float window, float eps, AfrParams prm,
-                                               const float4 *__restrict__ grad, const TilePartial *__restrict__ tiles,
-                                               float2 *__restrict__ sigma) {
-    int P = W * H;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
-        int x = p % W, y = p / W;
-        Widths w = widths(__ldg(grad + p), tile_volume(x, y, W, H, S, ntx, window, tiles), eps, prm);
-        sigma[p] = make_float2(w.ss, w.st);
-    }
-}
-
 __device__ __forceinline__ int half_width(int R, int dy) {
     int h = 0;
     while ((h + 1) * (h + 1) + dy * dy <= R * R) ++h;
@@ -102,20 +91,47 @@ __device__ __forceinline__ float shifted_exponent(const PixelFrame &f, float4 r)
     return fmaf(d2, f.ks, fmaf(r.z, f.kt, -f.m));
 }
 
-// Forward gather. One warp owns a 2x2 block of pixels. The bins of the union
-// of their four discs are enumerated first, with all lanes: each bin's record
-// range in the frame view and a 4-bit mask of the pixels whose disc holds it,
-// and the per-pixel exponent shifts. A prefix sum lays the bins' records out
-// in one index space; a per-warp map in shared memory lists, for each index,
-// the record and its mask. The gather then runs a flat loop: lane l takes
-// indices l, l+32, ... (two independent streams per iteration), so loads are
-// coalesced and every lane runs the same trip count whatever the bin
-// occupancy. A record outside a pixel's disc gets that pixel's exponent shift
-// -inf, i.e. weight 0. The arithmetic runs on pixel pairs (same row) with
-// paired FP32 instructions. Each lane accumulates the four pixels; the warp
-// reduces them at the end.
-constexpr int kMaxUnion = (2 * 8 + 2) * (2 * 8 + 2);   // union bins for R <= 8
-constexpr int kMapChunk = 512;                         // map entries per pass
+// Filter widths of every pixel (unless KEEP: the widths already in the map
+// are used) and the pixel's gather constants for the filter: -ks, -kt and the
+// exponent shift m.
+template <bool KEEP>
+__global__ void __launch_bounds__(256) k_sigma(int W, int H, int R, int S, int ntx, float window, float eps,
+                                               AfrParams prm, const float4 *__restrict__ grad,
+                                               const TilePartial *__restrict__ tiles,
+                                               const uint32_t *__restrict__ amin2, float2 *__restrict__ sigma,
+                                               float4 *__restrict__ fconst) {
+    int P = W * H;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        int x = p % W, y = p / W;
+        float2 sg;
+        if (KEEP) {
+            sg = sigma[p];
+        } else {
+            Widths w = widths(__ldg(grad + p), tile_volume(x, y, W, H, S, ntx, window, tiles), eps, prm);
+            sg = make_float2(w.ss, w.st);
+            sigma[p] = sg;
+        }
+        PixelFrame f = pixel_frame(x, y, W, H, R, sg, amin2);
+        fconst[p] = make_float4(-f.ks, -f.kt, f.m, 0.f);
+    }
+}
+
+// Forward gather. One warp owns a 2x2 block of pixels. The union of the four
+// discs is, row by row of bins, one contiguous run of columns, and the frame
+// view stores the records of consecutive bins of a row contiguously; so the
+// union's records are (2R + 2) contiguous index ranges. Lanes enumerate the
+// rows (range and count), a warp scan lays them out in one flat index space,
+// and the gather runs a flat loop over it: lane l takes flat indices l,
+// l + 32, ... (two independent streams per iteration), following its row with
+// a cursor, so loads are coalesced and every lane runs the same trip count
+// whatever the bin occupancy. A table in shared memory gives, for each
+// (row, column) of the union box, the exponent shift of each of the four
+// pixels, or -inf (weight 0) where the bin lies outside that pixel's disc;
+// a record's column is stored with it. The arithmetic runs on pixel pairs
+// (same row) with paired FP32 instructions. Each lane accumulates the four
+// pixels; the warp reduces them at the end. The per-pixel constants (-ks,
+// -kt, shift) come from k_sigma.
+constexpr int kMaxRows = 2 * 8 + 2;   // union rows (and columns) for R <= 8
 constexpr int kWarps = 8;
 
 typedef unsigned long long f2;   // two floats in one 64-bit register pair
@@ -147,12 +163,6 @@ __device__ __forceinline__ f2 mul2(f2 a, f2 b) {
     f2 d;
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
-}
-
-__device__ __forceinline__ float warp_min(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
 }
 
 __device__ __forceinline__ uint32_t warp_incl_scan_u(uint32_t v) {
@@ -204,29 +214,31 @@ __device__ __forceinline__ float warp_reduce16(float (&v)[16]) {
 // Pixel pair j (pixels (0, j) and (1, j)) constants and accumulators.
 struct PairConsts {
     f2 cx;         // (cx0, cx1)
-    float cy[2];   // row centres
+    f2 cy;         // (cy0, cy1): row centres
     f2 nks[2], nkt[2];
-    float m[4];    // exponent shift per pixel
 };
 struct PairAcc {
     f2 S[2], C[2], r[2], g[2], b[2];
 };
 
+// sh: the exponent shifts of the four pixels for the record's bin (-inf
+// outside a pixel's disc), pixel k = 2 j + column in component k.
 template <bool KAHAN>
-__device__ __forceinline__ void accumulate(const PairConsts &pc, uint32_t mask, float4 rec, float3 c, PairAcc &A) {
+__device__ __forceinline__ void accumulate(const PairConsts &pc, float4 sh, float4 rec, float3 c, PairAcc &A) {
     const f2 dx = sub2(pk(rec.x, rec.x), pc.cx);
     const f2 sx = mul2(dx, dx);
+    const f2 dy = sub2(pk(rec.y, rec.y), pc.cy);
+    const f2 sy = mul2(dy, dy);
+    float sy0, sy1;
+    upk(sy, sy0, sy1);
     const f2 a2 = pk(rec.z, rec.z);
     const f2 cr = pk(c.x, c.x), cg = pk(c.y, c.y), cb = pk(c.z, c.z);
+    const f2 m[2] = {pk(sh.x, sh.y), pk(sh.z, sh.w)};
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-        const float dy = rec.y - pc.cy[j];
-        const float sy = dy * dy;
-        const f2 d2 = add2(sx, pk(sy, sy));
-        // a record outside a pixel's disc gets exponent -inf: weight 0
-        const float m0 = (mask >> (2 * j)) & 1u ? pc.m[2 * j] : -INFINITY;
-        const float m1 = (mask >> (2 * j + 1)) & 1u ? pc.m[2 * j + 1] : -INFINITY;
-        const f2 e = fma2(d2, pc.nks[j], fma2(a2, pc.nkt[j], pk(m0, m1)));
+        const float syj = j ? sy1 : sy0;
+        const f2 d2 = add2(sx, pk(syj, syj));
+        const f2 e = fma2(d2, pc.nks[j], fma2(a2, pc.nkt[j], m[j]));
         float e0, e1;
         upk(e, e0, e1);
         const f2 w = pk(ex2(e0), ex2(e1));
@@ -244,172 +256,159 @@ __device__ __forceinline__ void accumulate(const PairConsts &pc, uint32_t mask, 
     }
 }
 
-// One 2x2 pixel block (top-left pixel bx, by) by one warp; smem holds the
-// warp's map and bin tables.
+// Per-warp shared memory of one 2x2 block.
 struct QuadSmem {
-    uint32_t map[kMapChunk];
-    uint32_t bin[kMaxUnion][2];   // (first record, index offset) per union bin
-    uint8_t bmask[kMaxUnion];
+    float4 shift[kMaxRows * kMaxRows];   // per (row, column) of the union box
+    uint32_t rstart[kMaxRows + 1];       // flat index of each row's first record; rstart[nv] = total
+    uint32_t rbase[kMaxRows];            // record index minus flat index within the row
 };
 
+// Row cursor of one gather stream: flat index j lies in union row v.
+struct Cursor {
+    int v, tb;            // row, shift-table offset of column 0 of the image
+    uint32_t end, base;   // flat end of row v, record index - flat index
+};
+
+__device__ __forceinline__ void advance(Cursor &k, uint32_t j, const QuadSmem &sm, int span, int colofs) {
+    while (j >= k.end) {
+        ++k.v;
+        k.end = sm.rstart[k.v + 1];
+        k.base = sm.rbase[k.v];
+        k.tb = k.v * span + colofs;
+    }
+}
+
+// One 2x2 pixel block (top-left pixel bx, by) by one warp.
 template <int CT, bool KAHAN, bool COHERENT = false>
-__device__ __forceinline__ void filter_block(int W, int H, int R, int bx, int by, const float2 *__restrict__ sigma,
-                                             const uint32_t *__restrict__ amin2, const uint32_t *__restrict__ foff,
-                                             const float4 *__restrict__ fpos, const void *__restrict__ fcol,
-                                             float4 *__restrict__ out, QuadSmem &sm) {
+__device__ __forceinline__ void filter_block(int W, int H, int R, int bx, int by, const float4 *__restrict__ fconst,
+                                             const uint32_t *__restrict__ foff, const float4 *__restrict__ fpos,
+                                             const void *__restrict__ fcol, float4 *__restrict__ out,
+                                             QuadSmem &sm) {
     using CS = ColorStore<CT>;
     const int lane = threadIdx.x & 31;
-    uint32_t *map = sm.map;
-    const int span = 2 * R + 2, nb = span * span;
-        float ks_l = 0.f, kt_l = 0.f;
-        if (lane < 4) {
-            int x = bx + (lane & 1), y = by + (lane >> 1);
-            if (x < W && y < H) {
-                // widths written earlier in the same launch are read through L2
-                float2 sgm = COHERENT ? __ldcg(sigma + (size_t)y * W + x) : __ldg(sigma + (size_t)y * W + x);
-                ks_l = kLog2e / (2.f * sgm.x * sgm.x);
-                kt_l = kLog2e / (2.f * sgm.y * sgm.y);
-            }
+    const int span = 2 * R + 2, nv = span;
+    const bool col1 = bx + 1 < W, row1 = by + 1 < H;
+    float4 fc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lane < 4) {
+        const int x = bx + (lane & 1), y = by + (lane >> 1);
+        if (x < W && y < H) {
+            // constants written earlier in the same launch are read through L2
+            fc = COHERENT ? __ldcg(fconst + (size_t)y * W + x) : __ldg(fconst + (size_t)y * W + x);
         }
-        float ks[4], kt[4];
-        bool valid[4];
+    }
+    float nks[4], nkt[4], mk[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        nks[k] = __shfl_sync(0xffffffffu, fc.x, k);
+        nkt[k] = __shfl_sync(0xffffffffu, fc.y, k);
+        mk[k] = __shfl_sync(0xffffffffu, fc.z, k);
+    }
+    // union rows: lane v (< nv) takes bin row by + v - R
+    uint32_t cnt = 0, first = 0;
+    if (lane < nv) {
+        const int v = lane - R, row = by + v;
+        const int h0 = (v >= -R && v <= R) ? half_width(R, v) : -1;
+        const int h1 = (row1 && v - 1 >= -R && v - 1 <= R) ? half_width(R, v - 1) : -1;
+        const int hm = max(h0, h1);
+        if (hm >= 0 && row >= 0 && row < H) {
+            const int c0 = max(0, bx - hm), c1 = min(W - 1, bx + (col1 ? 1 : 0) + hm);
+            const size_t q = (size_t)row * W;
+            first = __ldg(foff + q + c0);
+            cnt = __ldg(foff + q + c1 + 1) - first;
+        }
+    }
+    const uint32_t incl = warp_incl_scan_u(cnt);
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (lane < nv) {
+        sm.rstart[lane + 1] = incl;
+        sm.rbase[lane] = first - (incl - cnt);
+    }
+    if (lane == 0) sm.rstart[0] = 0;
+    // shift table: entry (v, u) of pixel k = (kx, ky) is its shift if
+    // (u - kx)^2 + (v - ky)^2 <= R^2 and the pixel lies in the image
+    const bool valid[4] = {true, col1, row1, col1 && row1};
+    for (int t = lane; t < nv * span; t += 32) {
+        const int v = t / span - R, u = t % span - R;
+        float s4[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            ks[k] = __shfl_sync(0xffffffffu, ks_l, k);
-            kt[k] = __shfl_sync(0xffffffffu, kt_l, k);
-            valid[k] = bx + (k & 1) < W && by + (k >> 1) < H;
+            const int du = u - (k & 1), dv = v - (k >> 1);
+            s4[k] = (valid[k] && du * du + dv * dv <= R * R) ? mk[k] : -INFINITY;
         }
-        // union bins: (v, u) in [-R, R+1]^2 relative to the block; a bin enters
-        // if some valid pixel's disc holds it; its records, mask and the
-        // per-pixel exponent shift candidates
-        float mm[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
-        uint32_t carry = 0;
-        for (int t0 = 0; t0 < nb; t0 += 32) {
-            const int t = t0 + lane;
-            uint32_t cnt = 0, first = 0, mask = 0;
-            if (t < nb) {
-                const int v = t / span - R, u = t % span - R;
-                const int row = by + v, col = bx + u;
-                if (row >= 0 && row < H && col >= 0 && col < W) {
+        sm.shift[t] = make_float4(s4[0], s4[1], s4[2], s4[3]);
+    }
+    __syncwarp();
+    PairConsts pc;
+    pc.cx = pk((float)bx + 0.5f, (float)bx + 1.5f);
+    pc.cy = pk((float)by + 0.5f, (float)by + 1.5f);
+    pc.nks[0] = pk(nks[0], nks[1]);
+    pc.nks[1] = pk(nks[2], nks[3]);
+    pc.nkt[0] = pk(nkt[0], nkt[1]);
+    pc.nkt[1] = pk(nkt[2], nkt[3]);
+    PairAcc A;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        int du = u - (k & 1), dv = v - (k >> 1);
-                        if (valid[k] && du * du + dv * dv <= R * R) mask |= 1u << k;
-                    }
-                    if (mask) {
-                        const size_t q = (size_t)row * W + col;
-                        first = __ldg(foff + q);
-                        cnt = __ldg(foff + q + 1) - first;
-                        if (cnt) {
-                            const float a2 = __uint_as_float(__ldg(amin2 + q));
+    for (int j = 0; j < 2; ++j) A.S[j] = A.C[j] = A.r[j] = A.g[j] = A.b[j] = 0ull;
+    const int colofs = R - bx;   // table column of image column qx: qx + colofs
+    Cursor ka{-1, 0, 0u, 0u}, kb{-1, 0, 0u, 0u};
+    uint32_t j = lane;
+    for (; j + 32 < total; j += 64) {
+        advance(ka, j, sm, span, colofs);
+        advance(kb, j + 32, sm, span, colofs);
+        const uint32_t ia = j + ka.base, ib = j + 32 + kb.base;
+        const float4 ra = __ldg(fpos + ia), rb = __ldg(fpos + ib);
+        const float3 ca = CS::load(fcol, ia), cbv = CS::load(fcol, ib);
+        const float4 sa = sm.shift[ka.tb + __float_as_int(ra.w)];
+        const float4 sb = sm.shift[kb.tb + __float_as_int(rb.w)];
+        accumulate<KAHAN>(pc, sa, ra, ca, A);
+        accumulate<KAHAN>(pc, sb, rb, cbv, A);
+    }
+    if (j < total) {
+        advance(ka, j, sm, span, colofs);
+        const uint32_t ia = j + ka.base;
+        const float4 ra = __ldg(fpos + ia);
+        accumulate<KAHAN>(pc, sm.shift[ka.tb + __float_as_int(ra.w)], ra, CS::load(fcol, ia), A);
+    }
+    float vals[16];
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                if (!((mask >> k) & 1u)) continue;
-                                float gx = bin_gap(u - (k & 1)), gy = bin_gap(v - (k >> 1));
-                                mm[k] = fminf(mm[k], fmaf(fmaf(gx, gx, gy * gy), ks[k], a2 * kt[k]));
-                            }
-                        }
-                    }
-                }
-            }
-            const uint32_t incl = warp_incl_scan_u(cnt);
-            if (t < nb) {
-                sm.bin[t][0] = first;
-                sm.bin[t][1] = carry + incl - cnt;
-                sm.bmask[t] = (uint8_t)mask;
-            }
-            carry += __shfl_sync(0xffffffffu, incl, 31);
-        }
-        const uint32_t total = carry;
-        PairConsts pc;
+    for (int jj = 0; jj < 2; ++jj) {
+        float a, b;
+        upk(KAHAN ? sub2(A.S[jj], A.C[jj]) : A.S[jj], a, b);
+        vals[2 * jj] = a;
+        vals[2 * jj + 1] = b;
+        upk(A.r[jj], a, b);
+        vals[4 + 2 * jj] = a;
+        vals[4 + 2 * jj + 1] = b;
+        upk(A.g[jj], a, b);
+        vals[8 + 2 * jj] = a;
+        vals[8 + 2 * jj + 1] = b;
+        upk(A.b[jj], a, b);
+        vals[12 + 2 * jj] = a;
+        vals[12 + 2 * jj + 1] = b;
+    }
+    const float tot = warp_reduce16(vals);
+    // value qq*4 + k (qq: S, r, g, b) of pixel k moves to lane k
+    float q[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            mm[k] = warp_min(mm[k]);
-            pc.m[k] = mm[k] < INFINITY ? mm[k] : 0.f;
+    for (int qq = 0; qq < 4; ++qq) {
+        const int want = qq * 4 + (lane & 3);
+        const int src = ((want >> 3) & 1) * 16 + ((want >> 2) & 1) * 8 + ((want >> 1) & 1) * 4 + (want & 1) * 2;
+        q[qq] = __shfl_sync(0xffffffffu, tot, src);
+    }
+    if (lane < 4 && bx + (lane & 1) < W && by + (lane >> 1) < H) {
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (q[0] > 0.f) {
+            const float inv = 1.f / q[0];
+            o = make_float4(q[1] * inv, q[2] * inv, q[3] * inv, q[0] * ex2(-fc.z));
         }
-        pc.cx = pk((float)bx + 0.5f, (float)bx + 1.5f);
-        pc.cy[0] = (float)by + 0.5f;
-        pc.cy[1] = (float)by + 1.5f;
-        pc.nks[0] = pk(-ks[0], -ks[1]);
-        pc.nks[1] = pk(-ks[2], -ks[3]);
-        pc.nkt[0] = pk(-kt[0], -kt[1]);
-        pc.nkt[1] = pk(-kt[2], -kt[3]);
-        __syncwarp();
-        PairAcc A;
-#pragma unroll
-        for (int j = 0; j < 2; ++j) A.S[j] = A.C[j] = A.r[j] = A.g[j] = A.b[j] = 0ull;
-        for (uint32_t w0 = 0; w0 < total; w0 += kMapChunk) {
-            const uint32_t w1 = min(total, w0 + (uint32_t)kMapChunk);
-            // map entries of this window: record index (28 bits) | pixel mask << 28
-            for (int t = lane; t < nb; t += 32) {
-                const uint32_t off = sm.bin[t][1];
-                const uint32_t next = (t + 1 < nb) ? sm.bin[t + 1][1] : total;
-                const uint32_t lo = max(off, w0), hi = min(next, w1);
-                if (lo >= hi) continue;
-                const uint32_t base = sm.bin[t][0] - off, tag = (uint32_t)sm.bmask[t] << 28;
-                for (uint32_t e = lo; e < hi; ++e) map[e - w0] = (base + e) | tag;
-            }
-            __syncwarp();
-            const uint32_t n = w1 - w0;
-            uint32_t j = lane;
-            for (; j + 32 < n; j += 64) {
-                const uint32_t ea = map[j], eb = map[j + 32];
-                const uint32_t ia = ea & 0x0FFFFFFFu, ib = eb & 0x0FFFFFFFu;
-                const float4 ra = __ldg(fpos + ia), rb = __ldg(fpos + ib);
-                const float3 ca = CS::load(fcol, ia), cbv = CS::load(fcol, ib);
-                accumulate<KAHAN>(pc, ea >> 28, ra, ca, A);
-                accumulate<KAHAN>(pc, eb >> 28, rb, cbv, A);
-            }
-            if (j < n) {
-                const uint32_t ea = map[j], ia = ea & 0x0FFFFFFFu;
-                accumulate<KAHAN>(pc, ea >> 28, __ldg(fpos + ia), CS::load(fcol, ia), A);
-            }
-            __syncwarp();
-        }
-        float vals[16];
-#pragma unroll
-        for (int jj = 0; jj < 2; ++jj) {
-            float a, b;
-            upk(KAHAN ? sub2(A.S[jj], A.C[jj]) : A.S[jj], a, b);
-            vals[2 * jj] = a;
-            vals[2 * jj + 1] = b;
-            upk(A.r[jj], a, b);
-            vals[4 + 2 * jj] = a;
-            vals[4 + 2 * jj + 1] = b;
-            upk(A.g[jj], a, b);
-            vals[8 + 2 * jj] = a;
-            vals[8 + 2 * jj + 1] = b;
-            upk(A.b[jj], a, b);
-            vals[12 + 2 * jj] = a;
-            vals[12 + 2 * jj + 1] = b;
-        }
-        const float tot = warp_reduce16(vals);
-        // value qq*4 + k (qq: S, r, g, b) of pixel k moves to lane k
-        float q[4];
-#pragma unroll
-        for (int qq = 0; qq < 4; ++qq) {
-            const int want = qq * 4 + (lane & 3);
-            const int src = ((want >> 3) & 1) * 16 + ((want >> 2) & 1) * 8 + ((want >> 1) & 1) * 4 + (want & 1) * 2;
-            q[qq] = __shfl_sync(0xffffffffu, tot, src);
-        }
-        if (lane < 4 && bx + (lane & 1) < W && by + (lane >> 1) < H) {
-            const int k = lane;
-            const float m = k == 0 ? pc.m[0] : k == 1 ? pc.m[1] : k == 2 ? pc.m[2] : pc.m[3];
-            float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (q[0] > 0.f) {
-                const float inv = 1.f / q[0];
-                o = make_float4(q[1] * inv, q[2] * inv, q[3] * inv, q[0] * ex2(-m));
-            }
-            out[(size_t)(by + (k >> 1)) * W + bx + (k & 1)] = o;
-        }
+        out[(size_t)(by + (lane >> 1)) * W + bx + (lane & 1)] = o;
+    }
     __syncwarp();
 }
 
 // Tile of (2 * tbx) x (2 * 32 / tbx) pixels per CTA: 32 blocks of 2x2, four
 // per warp.
 template <int CT, bool KAHAN>
-__global__ void __launch_bounds__(256, 3) k_filter(int W, int H, int R, int tbx, const float2 *__restrict__ sigma,
-                                                   const uint32_t *__restrict__ amin2,
+__global__ void __launch_bounds__(256, 3) k_filter(int W, int H, int R, int tbx, const float4 *__restrict__ fconst,
                                                    const uint32_t *__restrict__ foff, const float4 *__restrict__ fpos,
                                                    const void *__restrict__ fcol, float4 *__restrict__ out) {
     __shared__ QuadSmem smem[kWarps];
@@ -418,7 +417,7 @@ __global__ void __launch_bounds__(256, 3) k_filter(int W, int H, int R, int tbx,
     for (int blk = warp; blk < 32; blk += kWarps) {
         const int bx = blockIdx.x * 2 * tbx + (blk % tbx) * 2, by = blockIdx.y * 2 * tby + (blk / tbx) * 2;
         if (bx >= W || by >= H) continue;   // warp-uniform
-        filter_block<CT, KAHAN>(W, H, R, bx, by, sigma, amin2, foff, fpos, fcol, out, smem[warp]);
+        filter_block<CT, KAHAN>(W, H, R, bx, by, fconst, foff, fpos, fcol, out, smem[warp]);
     }
 }
 
@@ -454,7 +453,10 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchCtx *__restrict__ c
                 const int px = p % x.W, py = p / x.W;
                 Widths w = widths(__ldg(x.grad + p), tile_volume(px, py, x.W, x.H, x.S, x.ntx, x.window, x.tiles),
                                   x.eps, x.prm);
-                x.sigma[p] = make_float2(w.ss, w.st);
+                const float2 sg = make_float2(w.ss, w.st);
+                x.sigma[p] = sg;
+                const PixelFrame f = pixel_frame(px, py, x.W, x.H, x.R, sg, x.amin2);
+                x.fconst[p] = make_float4(-f.ks, -f.kt, f.m, 0.f);
             }
             __syncthreads();
             if (threadIdx.x == 0 && x.band0 + (uint32_t)k != skip_flag) {
@@ -488,8 +490,8 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchCtx *__restrict__ c
                 for (int blk = warp; blk < 32; blk += kWarps) {
                     const int bx = i * 2 * tbx + (blk % tbx) * 2, by = k * 2 * tby + (blk / tbx) * 2;
                     if (bx >= x.W || by >= x.H) continue;
-                    filter_block<CT, KAHAN, true>(x.W, x.H, x.R, bx, by, x.sigma, x.amin2, x.foff, x.fpos, x.fcol,
-                                                  x.out, smem[warp]);
+                    filter_block<CT, KAHAN, true>(x.W, x.H, x.R, bx, by, x.fconst, x.foff, x.fpos, x.fcol, x.out,
+                                                  smem[warp]);
                 }
             } else {
                 for (int t = threadIdx.x; t < 4 * 32; t += blockDim.x) {
@@ -654,9 +656,13 @@ const dim3 kQuadBlock(256);
 
 }  // namespace
 
-cudaError_t launch_sigma(AfrContext *c, const AfrParams *prm, cudaStream_t s) {
-    k_sigma<<<grid_for(c->P, 256), 256, 0, s>>>(c->W, c->H, c->S, c->ntx, c->cfg.window, c->cfg.eps_grad, *prm,
-                                                c->grad, c->tiles, c->sigma);
+cudaError_t launch_sigma(AfrContext *c, const AfrParams *prm, bool keep, cudaStream_t s) {
+#define AFR_SIGMA(K)                                                                                           \
+    k_sigma<K><<<grid_for(c->P, 256), 256, 0, s>>>(c->W, c->H, c->R, c->S, c->ntx, c->cfg.window, c->cfg.eps_grad, \
+                                                   *prm, c->grad, c->tiles, c->amin2, c->sigma, c->fconst)
+    if (keep) AFR_SIGMA(true);
+    else AFR_SIGMA(false);
+#undef AFR_SIGMA
     return cudaGetLastError();
 }
 
@@ -666,15 +672,15 @@ cudaError_t launch_filter(AfrContext *c, float t_now, float4 *out, cudaStream_t 
     dim3 grid((c->W + tw - 1) / tw, (c->H + th - 1) / th);
     switch (c->ct) {
         case AFR_F32:
-            k_filter<AFR_F32, false><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, tbx, c->sigma, c->amin2, c->foff,
+            k_filter<AFR_F32, false><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, tbx, c->fconst, c->foff,
                                                                    c->fpos, c->fcol, out);
             break;
         case AFR_F16:
-            k_filter<AFR_F16, true><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, tbx, c->sigma, c->amin2, c->foff,
+            k_filter<AFR_F16, true><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, tbx, c->fconst, c->foff,
                                                                   c->fpos, c->fcol, out);
             break;
         default:
-            k_filter<AFR_BF16, true><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, tbx, c->sigma, c->amin2, c->foff,
+            k_filter<AFR_BF16, true><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, tbx, c->fconst, c->foff,
                                                                    c->fpos, c->fcol, out);
             break;
     }
