@@ -209,7 +209,8 @@ static void free_batch(AfrContext *c) {
     void *ptrs[] = {c->bin_of, c->idx, c->pack};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    c->bin_of = c->idx = nullptr;
+    c->bin_of = nullptr;
+    c->idx = nullptr;
     c->pack = nullptr;
     c->batch_cap = 0;
 }

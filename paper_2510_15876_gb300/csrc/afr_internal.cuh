@@ -74,7 +74,7 @@ struct AfrContext {
     uint32_t *r_state = nullptr;  // count | head << 16
 
     // ingest scratch
-    uint32_t *bin_of = nullptr;   // [batch_cap] pixel of each sample (kInvalid: rejected)
+    uint2 *bin_of = nullptr;      // [batch_cap] (pixel, ticket within the pixel) of each sample (kInvalid: rejected)
     uint32_t *idx = nullptr;      // [batch_cap] batch indices sorted by pixel
     void *pack = nullptr;         // [batch_cap] samples repacked into aligned records
     size_t batch_cap = 0;

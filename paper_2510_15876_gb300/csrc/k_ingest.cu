@@ -1,13 +1,14 @@
 // k_ingest.cu -- section 4 deep buffer: counting-sort a batch of samples by
 // pixel and push each pixel's share into its queue of depth b.
 //
-//  1. hist:    validate each sample, record its pixel, count per pixel
-//              (warp-aggregated atomics; lanes hitting one pixel share one),
-//              and repack the sample into one aligned record (48 B for FP32
+//  1. hist:    validate each sample, record its pixel and its ticket (its
+//              rank among the pixel's samples in atomic order; warp-
+//              aggregated atomics: lanes hitting one pixel share one), and repack the sample into one aligned record (48 B for FP32
 //              colours, 32 B for 16-bit) so that the commit gathers one
 //              record instead of three scattered fields.
 //  2. scan:    pixel offsets of the batch's counting sort.
-//  3. scatter: write each sample's batch index into its pixel's segment.
+//  3. scatter: write each sample's batch index into its pixel's segment at
+//              offset + ticket (no atomics).
 //  4. commit:  one warp per pixel sorts the segment's indices (= insertion
 //              order) with a 32-lane bitonic network, keeps the min(b, m)
 //              newest, and writes them into the circular queue at
@@ -48,7 +49,7 @@ template <> struct Packed<AFR_BF16> : Packed16 {};
 template <int CT>
 __global__ void __launch_bounds__(256) k_hist(const float4 *__restrict__ pos, const void *__restrict__ col,
                                               const float2 *__restrict__ mo, uint32_t n, int W, int H,
-                                              uint32_t *__restrict__ bin_of, uint32_t *__restrict__ pcnt,
+                                              uint2 *__restrict__ bin_of, uint32_t *__restrict__ pcnt,
                                               Packed<CT> *__restrict__ pk, unsigned long long *__restrict__ dcount) {
     using CS = ColorStore<CT>;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -59,25 +60,23 @@ __global__ void __launch_bounds__(256) k_hist(const float4 *__restrict__ pos, co
         bool ok = isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(c.x) && isfinite(c.y) &&
                   isfinite(c.z) && isfinite(m.x) && isfinite(m.y) && p.x >= 0.f && p.y >= 0.f &&
                   p.x < (float)W && p.y < (float)H;
-        uint32_t bin = kInvalid;
-        if (ok) bin = (uint32_t)(int)floorf(p.y) * (uint32_t)W + (uint32_t)(int)floorf(p.x);
-        bin_of[i] = bin;
+        uint2 bt = make_uint2(kInvalid, 0u);
         if (ok) {
+            bt.x = (uint32_t)(int)floorf(p.y) * (uint32_t)W + (uint32_t)(int)floorf(p.x);
             Packed<CT>::store(pk + i, p, cr, m);
-            agg_inc(pcnt, bin);
+            bt.y = agg_inc(pcnt, bt.x);
         }
+        bin_of[i] = bt;
         agg_count(dcount + CNT_REJECTED, !ok);
     }
 }
 
-__global__ void __launch_bounds__(256) k_scatter(const uint32_t *__restrict__ bin_of, uint32_t n,
-                                                 const uint32_t *__restrict__ poff, uint32_t *__restrict__ pcur,
-                                                 uint32_t *__restrict__ idx) {
+__global__ void __launch_bounds__(256) k_scatter(const uint2 *__restrict__ bin_of, uint32_t n,
+                                                 const uint32_t *__restrict__ poff, uint32_t *__restrict__ idx) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        uint32_t bin = bin_of[i];
-        if (bin == kInvalid) continue;
-        uint32_t slot = poff[bin] + agg_inc(pcur, bin);
-        idx[slot] = i;
+        const uint2 bt = bin_of[i];
+        if (bt.x == kInvalid) continue;
+        idx[__ldg(poff + bt.x) + bt.y] = i;
     }
 }
 
@@ -163,8 +162,7 @@ cudaError_t run(AfrContext *c, const float4 *pos, const void *col, const float2 
     int g = grid_for(n, 256);
     k_hist<CT><<<g, 256, 0, s>>>(pos, col, mo, n, c->W, c->H, c->bin_of, c->pcnt, pk, c->dcount);
     if ((e = scan_exclusive(c->pcnt, c->poff, c->P, c->scan_tmp, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(c->pcnt, 0, sizeof(uint32_t) * c->P, s)) != cudaSuccess) return e;
-    k_scatter<<<g, 256, 0, s>>>(c->bin_of, n, c->poff, c->pcnt, c->idx);
+    k_scatter<<<g, 256, 0, s>>>(c->bin_of, n, c->poff, c->idx);
     int gc = grid_for((size_t)c->P * 32, 256);
     k_commit<CT><<<gc, 256, 0, s>>>(c->poff, c->idx, c->P, c->b, seq0, pk, c->r_xy, c->r_mo, c->r_t, c->r_depth,
                                     c->r_seq, c->r_col, c->r_state);
