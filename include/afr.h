@@ -248,6 +248,22 @@ AFR_API AfrStatus afr_reconstruct_ex(AfrContext *ctx, float t_now, const AfrPara
  * it does not change results). */
 AFR_API AfrStatus afr_set_tuning(AfrContext *ctx, int32_t radius, int32_t tile_bx);
 
+/* Kernel timing of the filter (instrumentation; the paper has no
+ * counterpart). While enabled, each afr_reconstruct / afr_reconstruct_ex
+ * records a pair of CUDA events on its stream around the filter kernel (the
+ * widths kernel before it is outside the pair), for up to
+ * AFR_PROFILE_MAX_LAUNCHES launches; later launches are not recorded.
+ * afr_profile_filter(ctx, 1) starts a new record (the context creates its
+ * events on first use), afr_profile_filter(ctx, 0) stops recording.
+ * afr_profile_read waits for the recorded events, writes up to cap launch
+ * durations in milliseconds to ms_host (host memory) in launch order, the
+ * number recorded to *count, and clears the record. Returns
+ * AFR_ERR_BAD_STATE if a stream was being captured into a CUDA graph when a
+ * pair would have been recorded (such a launch is not recorded). */
+enum { AFR_PROFILE_MAX_LAUNCHES = 256 };
+AFR_API AfrStatus afr_profile_filter(AfrContext *ctx, int32_t enable);
+AFR_API AfrStatus afr_profile_read(AfrContext *ctx, float *ms_host, int32_t cap, int32_t *count);
+
 /* ---------------------------------------------------------------------
  * Batched form: many independent viewer streams (contexts) reconstructed in
  * one persistent launch (no counterpart in the paper, which renders one

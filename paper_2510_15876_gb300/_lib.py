@@ -20,12 +20,14 @@ STATUS_NAMES = ["AFR_OK", "AFR_ERR_INVALID_ARG", "AFR_ERR_BAD_STATE", "AFR_ERR_O
 AFR_F32, AFR_F16, AFR_BF16 = 0, 1, 2
 AFR_MAP_LBAR, AFR_MAP_GX, AFR_MAP_GY, AFR_MAP_GT, AFR_MAP_SIGMA_S, AFR_MAP_SIGMA_T = range(6)
 AFR_RECON_KEEP_SIGMA = 1
+AFR_PROFILE_MAX_LAUNCHES = 256
 
 EXPORTED = [
     "afr_create", "afr_destroy", "afr_reset", "afr_reserve", "afr_insert_samples", "afr_estimate_gradients",
     "afr_reproject", "afr_reconstruct", "afr_reconstruct_ex", "afr_tile_feedback", "afr_reconstruct_backward",
     "afr_get_status", "afr_last_error", "afr_query", "afr_num_tiles", "afr_export_ring", "afr_export_frame",
     "afr_export_map", "afr_import_map", "afr_set_frame_colors", "afr_reproject_batch_static", "afr_set_tuning",
+    "afr_profile_filter", "afr_profile_read",
     "afr_batch_create", "afr_batch_destroy", "afr_batch_reconstruct", "afr_batch_inject_stall",
 ]
 
@@ -84,6 +86,8 @@ def _declare(L):
         "afr_reproject_batch_static": (S, [ctypes.POINTER(AfrSampleBatch), c_u32, c_i32, c_i32, c_i32, c_f32,
                                            c_p, c_p, c_p, c_p, c_p, c_p]),
         "afr_set_tuning": (S, [c_p, c_i32, c_i32]),
+        "afr_profile_filter": (S, [c_p, c_i32]),
+        "afr_profile_read": (S, [c_p, c_p, c_i32, ctypes.POINTER(c_i32)]),
         "afr_batch_create": (S, [ctypes.POINTER(c_p), c_i32, ctypes.POINTER(c_p)]),
         "afr_batch_destroy": (None, [c_p]),
         "afr_batch_reconstruct": (S, [c_p, c_f32, ctypes.POINTER(AfrParams), ctypes.POINTER(c_p), c_p]),

@@ -142,6 +142,17 @@ class Reconstructor:
         rgb = rgb.to(self.device, torch.float32).contiguous()
         self._check(self.lib.afr_set_frame_colors(self.h, _ptr(rgb), _stream(stream)))
 
+    def profile_filter(self, enable: bool = True):
+        """Start (or stop) recording the filter kernel's duration per reconstruct call."""
+        self._check(self.lib.afr_profile_filter(self.h, 1 if enable else 0))
+
+    def profile_read(self) -> list[float]:
+        """Durations (ms) of the filter launches recorded since profile_filter(True)."""
+        buf = (ctypes.c_float * L.AFR_PROFILE_MAX_LAUNCHES)()
+        n = ctypes.c_int32()
+        self._check(self.lib.afr_profile_read(self.h, buf, L.AFR_PROFILE_MAX_LAUNCHES, ctypes.byref(n)))
+        return [buf[k] for k in range(min(n.value, L.AFR_PROFILE_MAX_LAUNCHES))]
+
     # -- inspection ----------------------------------------------------------------
     def status(self) -> int:
         return self.lib.afr_get_status(self.h)

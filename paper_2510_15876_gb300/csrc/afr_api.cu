@@ -189,6 +189,10 @@ AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
 void afr_destroy(AfrContext *c) {
     if (!c) return;
     cudaDeviceSynchronize();
+    if (c->prof_ev) {
+        for (int k = 0; k < 2 * AFR_PROFILE_MAX_LAUNCHES; ++k) cudaEventDestroy(c->prof_ev[k]);
+        delete[] c->prof_ev;
+    }
     free_all(c);
     delete c;
 }
@@ -295,7 +299,19 @@ AfrStatus afr_reconstruct_ex(AfrContext *c, float t_now, const AfrParams *params
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
     e = afr::launch_sigma(c, params, keep, s);
+    cudaEvent_t *pair = nullptr;
+    if (e == cudaSuccess && c->prof_on && c->prof_n < AFR_PROFILE_MAX_LAUNCHES) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        e = cudaStreamIsCapturing(s, &cap);
+        if (e == cudaSuccess && cap != cudaStreamCaptureStatusNone) c->prof_capture_hit = true;
+        else if (e == cudaSuccess) pair = c->prof_ev + 2 * c->prof_n;
+    }
+    if (e == cudaSuccess && pair) e = cudaEventRecord(pair[0], s);
     if (e == cudaSuccess) e = afr::launch_filter(c, t_now, reinterpret_cast<float4 *>(out_rgbw_dev), s);
+    if (e == cudaSuccess && pair) {
+        e = cudaEventRecord(pair[1], s);
+        ++c->prof_n;
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "afr_reconstruct");
     c->recon_valid = true;
     c->recon_t = t_now;
@@ -496,6 +512,47 @@ AfrStatus afr_set_frame_colors(AfrContext *c, const float *rgb_dev, afr_stream_t
 }  // extern "C"
 
 extern "C" {
+
+AfrStatus afr_profile_filter(AfrContext *c, int32_t enable) {
+    if (!c) return AFR_ERR_INVALID_ARG;
+    if (enable && !c->prof_ev) {
+        c->prof_ev = new cudaEvent_t[2 * AFR_PROFILE_MAX_LAUNCHES]();
+        for (int k = 0; k < 2 * AFR_PROFILE_MAX_LAUNCHES; ++k) {
+            cudaError_t e = cudaEventCreate(&c->prof_ev[k]);
+            if (e != cudaSuccess) {
+                for (int j = 0; j < k; ++j) cudaEventDestroy(c->prof_ev[j]);
+                delete[] c->prof_ev;
+                c->prof_ev = nullptr;
+                return cuda_fail(c, e, "afr_profile_filter");
+            }
+        }
+    }
+    if (enable) {
+        c->prof_n = 0;
+        c->prof_capture_hit = false;
+    }
+    c->prof_on = enable != 0;
+    return AFR_OK;
+}
+
+AfrStatus afr_profile_read(AfrContext *c, float *ms, int32_t cap, int32_t *count) {
+    if (!c || !count || (cap > 0 && !ms) || cap < 0) return AFR_ERR_INVALID_ARG;
+    *count = 0;
+    const int n = c->prof_n;
+    for (int k = 0; k < n; ++k) {
+        cudaError_t e = cudaEventSynchronize(c->prof_ev[2 * k + 1]);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, c->prof_ev[2 * k], c->prof_ev[2 * k + 1]);
+        if (e != cudaSuccess) return cuda_fail(c, e, "afr_profile_read");
+        if (k < cap) ms[k] = t;
+    }
+    *count = n;
+    c->prof_n = 0;
+    const bool hit = c->prof_capture_hit;
+    c->prof_capture_hit = false;
+    if (hit) return fail(c, AFR_ERR_BAD_STATE, "afr_profile_read: launches under stream capture were not timed");
+    return AFR_OK;
+}
 
 AfrStatus afr_set_tuning(AfrContext *c, int32_t radius, int32_t tile_bx) {
     if (!c) return AFR_ERR_INVALID_ARG;

@@ -121,6 +121,10 @@ struct AfrContext {
     AfrParams recon_params{};
     bool sigma_imported = false;
     int tile_bx = 8;              // filter CTA tile: (2*tile_bx) x (64/tile_bx) pixels
+    // filter kernel timing (afr_profile_filter): event pairs, launches recorded
+    cudaEvent_t *prof_ev = nullptr;
+    bool prof_on = false, prof_capture_hit = false;
+    int prof_n = 0;
     std::string err;
 };
 
