@@ -49,7 +49,7 @@ typedef enum {
     AFR_ERR_BAD_STATE = 2,     /* calls out of order (see each call) */
     AFR_ERR_OOM = 3,           /* a device allocation failed */
     AFR_ERR_CUDA = 4,          /* a CUDA runtime call failed */
-    AFR_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out */
+    AFR_ERR_TIMEOUT = 5,       /* reserved: a bounded device-side wait ran out (no call waits) */
     AFR_ERR_DEVICE_CHECK = 6   /* a device-side consistency check failed */
 } AfrStatus;
 
@@ -276,23 +276,19 @@ typedef struct AfrBatch AfrBatch;
 AFR_API AfrStatus afr_batch_create(AfrContext *const *ctxs, int32_t n, AfrBatch **out);
 AFR_API void afr_batch_destroy(AfrBatch *batch);
 
-/* afr_reconstruct for every context in one launch: a persistent kernel takes
- * width items (one band of a context's width map) and then filter items (one
- * tile); a filter item waits, with a bounded spin of about 0.2 s, for its
- * band's widths. If the wait runs out the tile is written as zeros and
- * AFR_ERR_TIMEOUT is recorded in that context's status word (afr_get_status).
- * outs_dev[i] receives context i's image (as afr_reconstruct). Each context
- * needs afr_estimate_gradients and afr_reproject for t_now. The parameters
- * and output pointers are staged in pinned host memory owned by the batch, so
- * the call can be captured in a CUDA graph and replayed. */
+/* afr_reconstruct for every context of the batch in one call. Contexts of
+ * up to 131,072 pixels share two launches: one kernel computes the widths of
+ * all their pixels, then one persistent kernel takes tiles of any of them
+ * from a work queue (one atomic counter) and filters them; tiles never wait
+ * for one another. Larger contexts, which fill the GPU on their own, get
+ * afr_reconstruct's own launches within the call. Results equal
+ * afr_reconstruct's bit for bit. outs_dev[i] receives context i's image (as
+ * afr_reconstruct). Each context needs afr_estimate_gradients and
+ * afr_reproject for t_now. The parameters and output pointers are staged in
+ * pinned host memory owned by the batch, so the call can be captured in a
+ * CUDA graph and replayed. */
 AFR_API AfrStatus afr_batch_reconstruct(AfrBatch *batch, float t_now, const AfrParams *params,
                                         float *const *outs_dev, afr_stream_t stream);
-
-/* Fault injection for testing the bounded wait: until called again with -1,
- * the width items of band `band` of context `ctx_index` (caller's index)
- * leave their flag unset, so the filter items of that band run out their
- * wait. */
-AFR_API AfrStatus afr_batch_inject_stall(AfrBatch *batch, int32_t ctx_index, int32_t band);
 
 /* ---------------------------------------------------------------------
  * Allocation-free variant (no counterpart in the paper).

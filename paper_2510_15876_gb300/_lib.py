@@ -28,7 +28,7 @@ EXPORTED = [
     "afr_get_status", "afr_last_error", "afr_query", "afr_num_tiles", "afr_export_ring", "afr_export_frame",
     "afr_export_map", "afr_import_map", "afr_set_frame_colors", "afr_reproject_batch_static", "afr_set_tuning",
     "afr_profile_filter", "afr_profile_read",
-    "afr_batch_create", "afr_batch_destroy", "afr_batch_reconstruct", "afr_batch_inject_stall",
+    "afr_batch_create", "afr_batch_destroy", "afr_batch_reconstruct",
 ]
 
 
@@ -91,7 +91,6 @@ def _declare(L):
         "afr_batch_create": (S, [ctypes.POINTER(c_p), c_i32, ctypes.POINTER(c_p)]),
         "afr_batch_destroy": (None, [c_p]),
         "afr_batch_reconstruct": (S, [c_p, c_f32, ctypes.POINTER(AfrParams), ctypes.POINTER(c_p), c_p]),
-        "afr_batch_inject_stall": (S, [c_p, c_i32, c_i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

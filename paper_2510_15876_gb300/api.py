@@ -232,11 +232,6 @@ class BatchReconstructor:
             raise L.AfrError(st, "afr_batch_reconstruct failed")
         return self.outs
 
-    def inject_stall(self, ctx_index: int, band: int):
-        st = self.lib.afr_batch_inject_stall(self.h, ctx_index, band)
-        if st != L.AFR_OK:
-            raise L.AfrError(st, "afr_batch_inject_stall failed")
-
     def close(self):
         if getattr(self, "h", None):
             self.lib.afr_batch_destroy(self.h)

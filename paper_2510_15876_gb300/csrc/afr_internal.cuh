@@ -50,8 +50,8 @@ struct BatchCtx {
     const void *fcol;
     float4 *out;
     uint32_t *derr;
-    uint32_t band0;     // first band flag of this context
-    uint32_t a0, b0;    // first width item, first filter item (filter items counted from 0)
+    uint32_t a0;        // first work item (tile) of this context
+    uint32_t s0;        // first width chunk of this context
 };
 
 }  // namespace afr
@@ -75,8 +75,7 @@ struct AfrContext {
 
     // ingest scratch
     uint2 *bin_of = nullptr;      // [batch_cap] (pixel, ticket within the pixel) of each sample (kInvalid: rejected)
-    uint32_t *idx = nullptr;      // [batch_cap] batch indices sorted by pixel
-    void *pack = nullptr;         // [batch_cap] samples repacked into aligned records
+    void *pack = nullptr;         // [batch_cap] 64-byte sample records in pixel order
     size_t batch_cap = 0;
     uint32_t *pcnt = nullptr;     // [P]
     uint32_t *poff = nullptr;     // [P+1]
@@ -221,9 +220,11 @@ cudaError_t launch_backward(AfrContext *c, const float4 *grad_rgb, float *grad_c
                             cudaStream_t s);
 cudaError_t launch_set_frame_colors(AfrContext *c, const float *rgb, cudaStream_t s);
 int backward_blocks(int W, int H);
-cudaError_t launch_batch(int ct, const BatchCtx *cs, int nctx, uint32_t totalA, uint32_t total, uint32_t *queue,
-                         uint32_t *flags, uint32_t skip_flag, long long wait_cycles, int grid, cudaStream_t s);
+cudaError_t launch_batch(int ct, const BatchCtx *cs, int nctx, uint32_t nchunks, uint32_t total, uint32_t *queue,
+                         int grid, cudaStream_t s);
 size_t packed_bytes(int ct);
+constexpr int kBatchSigmaChunk = 2048;   // pixels per width chunk of a batched launch
+constexpr int kBatchDirectPixels = 131072;   // larger contexts of a batch get their own launches
 cudaError_t launch_resident_count(AfrContext *c, cudaStream_t s);
 
 }  // namespace afr

@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(256) k_sigma(int W, int H, int R, int S, int n
 // -kt, shift) come from k_sigma.
 constexpr int kMaxRows = 2 * 8 + 2;   // union rows (and columns) for R <= 8
 constexpr int kWarps = 8;
+constexpr int kMaxBatch = 64;         // contexts per batched launch
 
 typedef unsigned long long f2;   // two floats in one 64-bit register pair
 
@@ -279,7 +280,7 @@ __device__ __forceinline__ void advance(Cursor &k, uint32_t j, const QuadSmem &s
 }
 
 // One 2x2 pixel block (top-left pixel bx, by) by one warp.
-template <int CT, bool KAHAN, bool COHERENT = false>
+template <int CT, bool KAHAN>
 __device__ __forceinline__ void filter_block(int W, int H, int R, int bx, int by, const float4 *__restrict__ fconst,
                                              const uint32_t *__restrict__ foff, const float4 *__restrict__ fpos,
                                              const void *__restrict__ fcol, float4 *__restrict__ out,
@@ -291,10 +292,7 @@ __device__ __forceinline__ void filter_block(int W, int H, int R, int bx, int by
     float4 fc = make_float4(0.f, 0.f, 0.f, 0.f);
     if (lane < 4) {
         const int x = bx + (lane & 1), y = by + (lane >> 1);
-        if (x < W && y < H) {
-            // constants written earlier in the same launch are read through L2
-            fc = COHERENT ? __ldcg(fconst + (size_t)y * W + x) : __ldg(fconst + (size_t)y * W + x);
-        }
+        if (x < W && y < H) fc = __ldg(fconst + (size_t)y * W + x);
     }
     float nks[4], nkt[4], mk[4];
 #pragma unroll
@@ -421,84 +419,80 @@ __global__ void __launch_bounds__(256, 3) k_filter(int W, int H, int R, int tbx,
     }
 }
 
-// ---- batched persistent launch ----------------------------------------------
-// One launch reconstructs many contexts. A work queue (one atomic counter)
-// hands out, first, width items (one band of th rows of one context: the
-// width map of the band, then a release flag) and then filter items (one
-// tw x th tile). A filter item waits for its band's flag with a bounded spin
-// (clock-limited, with back-off); if the limit passes it records ERR_TIMEOUT
-// in its context's status word, writes zeros for the tile and moves on, so
-// the launch always ends. Items are taken in queue order, so a filter item
-// only ever waits for a width item already taken by a running CTA.
-template <int CT, bool KAHAN>
-__global__ void __launch_bounds__(256, 3) k_batch(const BatchCtx *__restrict__ cs, int nctx, uint32_t totalA,
-                                                  uint32_t total, uint32_t *queue, uint32_t *flags,
-                                                  uint32_t skip_flag, long long wait_cycles) {
-    __shared__ QuadSmem smem[kWarps];
-    __shared__ uint32_t item_sh;
-    __shared__ int ok_sh;
-    const int warp = threadIdx.x >> 5;
-    for (;;) {
-        if (threadIdx.x == 0) item_sh = atomicAdd(queue, 1u);
+// ---- batched form ---------------------------------------------------------------
+// Two launches reconstruct many contexts. k_batch_sigma computes the widths
+// and gather constants of every pixel of every context (thread per pixel,
+// full occupancy: the per-pixel work is bound by the latency of the footprint
+// loads). k_batch, a persistent kernel, then takes tiles of (2 tbx) x
+// (64 / tbx) pixels of any context from a work queue (one atomic counter, the
+// next tile claimed while the current one runs), largest contexts first, and
+// filters them. Tiles never wait for one another.
+
+// owning context of a batch-wide index: the last c with first[c] <= v
+__device__ __forceinline__ int batch_owner(const uint32_t *first, int nctx, uint32_t v) {
+    int lo = 0, hi = nctx - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Widths of every pixel of the batch: each block takes chunks of
+// kBatchSigmaChunk pixels of one context (chunks are numbered per context from
+// BatchCtx::s0) and reads the context's record once per chunk.
+__global__ void __launch_bounds__(256) k_batch_sigma(const BatchCtx *__restrict__ cs, int nctx, uint32_t nchunks) {
+    __shared__ uint32_t first[kMaxBatch];      // first chunk of each context
+    __shared__ BatchCtx ctx;
+    for (int c = threadIdx.x; c < nctx; c += blockDim.x) first[c] = cs[c].s0;
+    __syncthreads();
+    for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        if (threadIdx.x == 0) ctx = cs[batch_owner(first, nctx, ch)];
         __syncthreads();
-        const uint32_t item = item_sh;
+        const int W = ctx.W, H = ctx.H, P = W * H;
+        const int p0 = (int)(ch - ctx.s0) * kBatchSigmaChunk, p1 = min(P, p0 + kBatchSigmaChunk);
+        for (int p = p0 + (int)threadIdx.x; p < p1; p += blockDim.x) {
+            const int px = p % W, py = p / W;
+            Widths w = widths(__ldg(ctx.grad + p), tile_volume(px, py, W, H, ctx.S, ctx.ntx, ctx.window, ctx.tiles),
+                              ctx.eps, ctx.prm);
+            const float2 sg = make_float2(w.ss, w.st);
+            ctx.sigma[p] = sg;
+            const PixelFrame f = pixel_frame(px, py, W, H, ctx.R, sg, ctx.amin2);
+            ctx.fconst[p] = make_float4(-f.ks, -f.kt, f.m, 0.f);
+        }
+        __syncthreads();
+    }
+}
+
+template <int CT, bool KAHAN>
+__global__ void __launch_bounds__(256, 3) k_batch(const BatchCtx *__restrict__ cs, int nctx, uint32_t total,
+                                                  uint32_t *queue) {
+    // shared memory: the per-warp tables and two words, so that three CTAs
+    // fit the 132 KB shared-memory carve-out and leave the rest to L1
+    __shared__ QuadSmem smem[kWarps];
+    __shared__ uint32_t item_buf[2];            // current and next claimed tile
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) item_buf[0] = atomicAdd(queue, 1u);
+    __syncthreads();
+    for (int it = 0;; ++it) {
+        const uint32_t item = item_buf[it & 1];
         if (item >= total) break;
-        if (item < totalA) {
-            int c = 0;
-            while (c + 1 < nctx && cs[c + 1].a0 <= item) ++c;
-            const BatchCtx &x = cs[c];
-            const int k = (int)(item - x.a0);
-            const int y0 = k * x.th, y1 = min(x.H, y0 + x.th);
-            for (int p = y0 * x.W + threadIdx.x; p < y1 * x.W; p += blockDim.x) {
-                const int px = p % x.W, py = p / x.W;
-                Widths w = widths(__ldg(x.grad + p), tile_volume(px, py, x.W, x.H, x.S, x.ntx, x.window, x.tiles),
-                                  x.eps, x.prm);
-                const float2 sg = make_float2(w.ss, w.st);
-                x.sigma[p] = sg;
-                const PixelFrame f = pixel_frame(px, py, x.W, x.H, x.R, sg, x.amin2);
-                x.fconst[p] = make_float4(-f.ks, -f.kt, f.m, 0.f);
-            }
-            __syncthreads();
-            if (threadIdx.x == 0 && x.band0 + (uint32_t)k != skip_flag) {
-                __threadfence();
-                atomicExch(flags + x.band0 + k, 1u);
-            }
-        } else {
-            const uint32_t j = item - totalA;
-            int c = 0;
-            while (c + 1 < nctx && cs[c + 1].b0 <= j) ++c;
-            const BatchCtx &x = cs[c];
-            const uint32_t local = j - x.b0;
-            const int k = (int)(local / (uint32_t)x.ntiles_x), i = (int)(local % (uint32_t)x.ntiles_x);
-            if (threadIdx.x == 0) {
-                const long long t0 = clock64();
-                int ok = 1;
-                while (atomicAdd(flags + x.band0 + k, 0u) == 0u) {
-                    if (clock64() - t0 > wait_cycles) {
-                        ok = 0;
-                        atomicOr(x.derr, ERR_TIMEOUT);
-                        break;
-                    }
-                    __nanosleep(256);
-                }
-                __threadfence();
-                ok_sh = ok;
-            }
-            __syncthreads();
-            const int tbx = x.tbx, tby = 32 / tbx;
-            if (ok_sh) {
-                for (int blk = warp; blk < 32; blk += kWarps) {
-                    const int bx = i * 2 * tbx + (blk % tbx) * 2, by = k * 2 * tby + (blk / tbx) * 2;
-                    if (bx >= x.W || by >= x.H) continue;
-                    filter_block<CT, KAHAN, true>(x.W, x.H, x.R, bx, by, x.fconst, x.foff, x.fpos, x.fcol, x.out,
-                                                  smem[warp]);
-                }
-            } else {
-                for (int t = threadIdx.x; t < 4 * 32; t += blockDim.x) {
-                    const int px = i * 2 * tbx + t % (2 * tbx), py = k * 2 * tby + t / (2 * tbx);
-                    if (px < x.W && py < x.H) x.out[(size_t)py * x.W + px] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            }
+        if (threadIdx.x == 0) item_buf[(it + 1) & 1] = atomicAdd(queue, 1u);
+        int lo = 0, hi = nctx - 1;                  // owning context: last c with cs[c].a0 <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&cs[mid].a0) <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchCtx &x = cs[lo];
+        const uint32_t local = item - x.a0;
+        const int band = (int)(local / (uint32_t)x.ntiles_x), tile = (int)(local % (uint32_t)x.ntiles_x);
+        const int tbx = x.tbx, tw = 2 * tbx, th = 2 * (32 / tbx);
+        for (int blk = warp; blk < 32; blk += kWarps) {
+            const int bx = tile * tw + (blk % tbx) * 2, by = band * th + (blk / tbx) * 2;
+            if (bx >= x.W || by >= x.H) continue;
+            filter_block<CT, KAHAN>(x.W, x.H, x.R, bx, by, x.fconst, x.foff, x.fpos, x.fcol, x.out, smem[warp]);
         }
         __syncthreads();
     }
@@ -673,15 +667,15 @@ cudaError_t launch_filter(AfrContext *c, float t_now, float4 *out, cudaStream_t 
     switch (c->ct) {
         case AFR_F32:
             k_filter<AFR_F32, false><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, tbx, c->fconst, c->foff,
-                                                                   c->fpos, c->fcol, out);
+                                                                     c->fpos, c->fcol, out);
             break;
         case AFR_F16:
             k_filter<AFR_F16, true><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, tbx, c->fconst, c->foff,
-                                                                  c->fpos, c->fcol, out);
+                                                                    c->fpos, c->fcol, out);
             break;
         default:
             k_filter<AFR_BF16, true><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, tbx, c->fconst, c->foff,
-                                                                   c->fpos, c->fcol, out);
+                                                                     c->fpos, c->fcol, out);
             break;
     }
     return cudaGetLastError();
@@ -720,21 +714,13 @@ cudaError_t launch_set_frame_colors(AfrContext *c, const float *rgb, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch(int ct, const BatchCtx *cs, int nctx, uint32_t totalA, uint32_t total, uint32_t *queue,
-                         uint32_t *flags, uint32_t skip_flag, long long wait_cycles, int grid, cudaStream_t s) {
+cudaError_t launch_batch(int ct, const BatchCtx *cs, int nctx, uint32_t nchunks, uint32_t total, uint32_t *queue,
+                         int grid, cudaStream_t s) {
+    k_batch_sigma<<<grid_for((size_t)nchunks * 256, 256), 256, 0, s>>>(cs, nctx, nchunks);
     switch (ct) {
-        case AFR_F32:
-            k_batch<AFR_F32, false><<<grid, kQuadBlock, 0, s>>>(cs, nctx, totalA, total, queue, flags, skip_flag,
-                                                                wait_cycles);
-            break;
-        case AFR_F16:
-            k_batch<AFR_F16, true><<<grid, kQuadBlock, 0, s>>>(cs, nctx, totalA, total, queue, flags, skip_flag,
-                                                               wait_cycles);
-            break;
-        default:
-            k_batch<AFR_BF16, true><<<grid, kQuadBlock, 0, s>>>(cs, nctx, totalA, total, queue, flags, skip_flag,
-                                                                wait_cycles);
-            break;
+        case AFR_F32: k_batch<AFR_F32, false><<<grid, kQuadBlock, 0, s>>>(cs, nctx, total, queue); break;
+        case AFR_F16: k_batch<AFR_F16, true><<<grid, kQuadBlock, 0, s>>>(cs, nctx, total, queue); break;
+        default: k_batch<AFR_BF16, true><<<grid, kQuadBlock, 0, s>>>(cs, nctx, total, queue); break;
     }
     return cudaGetLastError();
 }

@@ -1,56 +1,73 @@
 // k_ingest.cu -- section 4 deep buffer: counting-sort a batch of samples by
 // pixel and push each pixel's share into its queue of depth b.
 //
-//  1. hist:    validate each sample, record its pixel and its ticket (its
-//              rank among the pixel's samples in atomic order; warp-
-//              aggregated atomics: lanes hitting one pixel share one), and repack the sample into one aligned record (48 B for FP32
-//              colours, 32 B for 16-bit) so that the commit gathers one
-//              record instead of three scattered fields.
-//  2. scan:    pixel offsets of the batch's counting sort.
-//  3. scatter: write each sample's batch index into its pixel's segment at
-//              offset + ticket (no atomics).
-//  4. commit:  one warp per pixel sorts the segment's indices (= insertion
-//              order) with a 32-lane bitonic network, keeps the min(b, m)
-//              newest, and writes them into the circular queue at
-//              (head + rank) mod b, the slots sequential pushes would use.
+//  1. hist:   validate each sample, record its pixel and its ticket (its rank
+//             among the pixel's samples in atomic order; warp-aggregated
+//             atomics: lanes hitting one pixel share one).
+//  2. scan:   pixel offsets of the counting sort.
+//  3. place:  write each sample, repacked into one 64-byte record that also
+//             carries its batch index, at offset + ticket. A warp stages its
+//             32 records in shared memory and stores them back four lanes per
+//             record, so every record is one whole 64-byte block (no partial
+//             sectors for the memory system to merge).
+//  4. commit: one warp per pixel reads the pixel's records (contiguous),
+//             sorts their batch indices (= insertion order) with a 32-lane
+//             bitonic network, keeps the min(b, m) newest and writes them into
+//             the circular queue at (head + rank) mod b, the slots sequential
+//             pushes would use.
 #include "afr_internal.cuh"
 
 namespace afr {
 namespace {
 
-// Packed sample: a = (x, y, t, depth); colour and motion follow (layout per type).
-template <int CT> struct Packed;
-template <> struct Packed<AFR_F32> {
-    float4 a, b, c;   // b = (r, g, b, mx), c = (my, -, -, -)
-    static __device__ __forceinline__ void store(Packed *dst, float4 p, float4 col, float2 m) {
-        dst->a = p;
-        dst->b = make_float4(col.x, col.y, col.z, m.x);
-        dst->c = make_float4(m.y, 0.f, 0.f, 0.f);
-    }
-    __device__ __forceinline__ float4 color() const { return make_float4(b.x, b.y, b.z, 0.f); }
-    __device__ __forceinline__ float2 motion() const { return make_float2(b.w, c.x); }
+// 64-byte staging record: a = (x, y, t, depth); b = colour and motion;
+// c.y = batch index. F32: b = (r, g, b, m_x), c.x = m_y. 16-bit colours:
+// b = (r | g << 16, b, m_x, m_y).
+struct alignas(64) Rec64 {
+    uint4 a, b, c, d;
 };
-struct Packed16 {
-    float4 a;
-    uint4 b;          // (r | g << 16, b, mx bits, my bits)
-    static __device__ __forceinline__ void store(Packed16 *dst, float4 p, ushort4 col, float2 m) {
-        dst->a = p;
-        dst->b = make_uint4((uint32_t)col.x | ((uint32_t)col.y << 16), (uint32_t)col.z, __float_as_uint(m.x),
-                            __float_as_uint(m.y));
+
+template <int CT> struct RecCodec;
+template <> struct RecCodec<AFR_F32> {
+    using T = float4;
+    static __device__ __forceinline__ void pack(Rec64 &r, float4 p, T col, float2 m, uint32_t i) {
+        r.a = make_uint4(__float_as_uint(p.x), __float_as_uint(p.y), __float_as_uint(p.z), __float_as_uint(p.w));
+        r.b = make_uint4(__float_as_uint(col.x), __float_as_uint(col.y), __float_as_uint(col.z),
+                         __float_as_uint(m.x));
+        r.c = make_uint4(__float_as_uint(m.y), i, 0u, 0u);
+        r.d = make_uint4(0u, 0u, 0u, 0u);
     }
-    __device__ __forceinline__ ushort4 color() const {
+    static __device__ __forceinline__ T color(uint4 b, uint4) {
+        return make_float4(__uint_as_float(b.x), __uint_as_float(b.y), __uint_as_float(b.z), 0.f);
+    }
+    static __device__ __forceinline__ float2 motion(uint4 b, uint4 c) {
+        return make_float2(__uint_as_float(b.w), __uint_as_float(c.x));
+    }
+};
+struct RecCodec16 {
+    using T = ushort4;
+    static __device__ __forceinline__ void pack(Rec64 &r, float4 p, T col, float2 m, uint32_t i) {
+        r.a = make_uint4(__float_as_uint(p.x), __float_as_uint(p.y), __float_as_uint(p.z), __float_as_uint(p.w));
+        r.b = make_uint4((uint32_t)col.x | ((uint32_t)col.y << 16), (uint32_t)col.z, __float_as_uint(m.x),
+                         __float_as_uint(m.y));
+        r.c = make_uint4(0u, i, 0u, 0u);
+        r.d = make_uint4(0u, 0u, 0u, 0u);
+    }
+    static __device__ __forceinline__ T color(uint4 b, uint4) {
         return make_ushort4((unsigned short)(b.x & 0xFFFFu), (unsigned short)(b.x >> 16), (unsigned short)b.y, 0);
     }
-    __device__ __forceinline__ float2 motion() const { return make_float2(__uint_as_float(b.z), __uint_as_float(b.w)); }
+    static __device__ __forceinline__ float2 motion(uint4 b, uint4) {
+        return make_float2(__uint_as_float(b.z), __uint_as_float(b.w));
+    }
 };
-template <> struct Packed<AFR_F16> : Packed16 {};
-template <> struct Packed<AFR_BF16> : Packed16 {};
+template <> struct RecCodec<AFR_F16> : RecCodec16 {};
+template <> struct RecCodec<AFR_BF16> : RecCodec16 {};
 
 template <int CT>
 __global__ void __launch_bounds__(256) k_hist(const float4 *__restrict__ pos, const void *__restrict__ col,
                                               const float2 *__restrict__ mo, uint32_t n, int W, int H,
                                               uint2 *__restrict__ bin_of, uint32_t *__restrict__ pcnt,
-                                              Packed<CT> *__restrict__ pk, unsigned long long *__restrict__ dcount) {
+                                              unsigned long long *__restrict__ dcount) {
     using CS = ColorStore<CT>;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         float4 p = __ldg(pos + i);
@@ -63,7 +80,6 @@ __global__ void __launch_bounds__(256) k_hist(const float4 *__restrict__ pos, co
         uint2 bt = make_uint2(kInvalid, 0u);
         if (ok) {
             bt.x = (uint32_t)(int)floorf(p.y) * (uint32_t)W + (uint32_t)(int)floorf(p.x);
-            Packed<CT>::store(pk + i, p, cr, m);
             bt.y = agg_inc(pcnt, bt.x);
         }
         bin_of[i] = bt;
@@ -71,23 +87,58 @@ __global__ void __launch_bounds__(256) k_hist(const float4 *__restrict__ pos, co
     }
 }
 
-__global__ void __launch_bounds__(256) k_scatter(const uint2 *__restrict__ bin_of, uint32_t n,
-                                                 const uint32_t *__restrict__ poff, uint32_t *__restrict__ idx) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint2 bt = bin_of[i];
-        if (bt.x == kInvalid) continue;
-        idx[__ldg(poff + bt.x) + bt.y] = i;
+// Each warp takes 32 consecutive samples: lanes build their records in
+// shared memory (80-byte stride: conflict-free 16-byte accesses), then lane
+// 4k + q stores part q of record 8r + k in round r.
+constexpr int kPlaceWarps = 8;
+
+template <int CT>
+__global__ void __launch_bounds__(32 * kPlaceWarps) k_place(const float4 *__restrict__ pos,
+                                                            const void *__restrict__ col,
+                                                            const float2 *__restrict__ mo, uint32_t n,
+                                                            const uint2 *__restrict__ bin_of,
+                                                            const uint32_t *__restrict__ poff,
+                                                            Rec64 *__restrict__ pk) {
+    using CS = ColorStore<CT>;
+    __shared__ uint4 stage[kPlaceWarps][32][5];
+    __shared__ uint32_t dest[kPlaceWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t nwarps = gridDim.x * kPlaceWarps;
+    for (uint32_t base = (blockIdx.x * kPlaceWarps + w) * 32u; base < n; base += nwarps * 32u) {
+        const uint32_t i = base + lane;
+        uint32_t d = kInvalid;
+        if (i < n) {
+            const uint2 bt = bin_of[i];
+            if (bt.x != kInvalid) {
+                d = __ldg(poff + bt.x) + bt.y;
+                Rec64 r;
+                RecCodec<CT>::pack(r, __ldg(pos + i), CS::raw(col, i), __ldg(mo + i), i);
+                stage[w][lane][0] = r.a;
+                stage[w][lane][1] = r.b;
+                stage[w][lane][2] = r.c;
+                stage[w][lane][3] = r.d;
+            }
+        }
+        dest[w][lane] = d;
+        __syncwarp();
+#pragma unroll
+        for (int round = 0; round < 4; ++round) {
+            const int k = round * 8 + (lane >> 2), q = lane & 3;
+            const uint32_t dk = dest[w][k];
+            if (dk != kInvalid) reinterpret_cast<uint4 *>(pk + dk)[q] = stage[w][k][q];
+        }
+        __syncwarp();
     }
 }
 
-// ascending bitonic sort of one key per lane across a full warp
-__device__ __forceinline__ uint32_t warp_sort_asc(uint32_t v) {
+// ascending bitonic sort of one 64-bit key per lane across a full warp
+__device__ __forceinline__ unsigned long long warp_sort_asc(unsigned long long v) {
     int lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
         for (int j = k >> 1; j > 0; j >>= 1) {
-            uint32_t o = __shfl_xor_sync(0xffffffffu, v, j);
+            unsigned long long o = __shfl_xor_sync(0xffffffffu, v, j);
             bool up = ((lane & k) == 0);
             bool lower = ((lane & j) == 0);
             v = (lower == up) ? min(v, o) : max(v, o);
@@ -97,57 +148,63 @@ __device__ __forceinline__ uint32_t warp_sort_asc(uint32_t v) {
 }
 
 // merge step of a bitonic sequence held across the warp into ascending order
-__device__ __forceinline__ uint32_t warp_merge_asc(uint32_t v) {
+__device__ __forceinline__ unsigned long long warp_merge_asc(unsigned long long v) {
     int lane = threadIdx.x & 31;
 #pragma unroll
     for (int j = 16; j > 0; j >>= 1) {
-        uint32_t o = __shfl_xor_sync(0xffffffffu, v, j);
+        unsigned long long o = __shfl_xor_sync(0xffffffffu, v, j);
         v = ((lane & j) == 0) ? min(v, o) : max(v, o);
     }
     return v;
 }
 
+// sort key of record e of a pixel's segment: (batch index + 1) << 32 | position
+__device__ __forceinline__ unsigned long long rec_key(const Rec64 *__restrict__ pk, uint32_t beg, uint32_t e) {
+    const uint32_t i = __ldg(&pk[beg + e].c.y);
+    return ((unsigned long long)(i + 1u) << 32) | e;
+}
+
 template <int CT>
-__global__ void __launch_bounds__(256) k_commit(const uint32_t *__restrict__ poff, const uint32_t *__restrict__ idx,
-                                                int P, int b, uint32_t seq0, const Packed<CT> *__restrict__ pk,
-                                                float2 *__restrict__ r_xy, float2 *__restrict__ r_mo,
-                                                float *__restrict__ r_t, float *__restrict__ r_depth,
-                                                uint32_t *__restrict__ r_seq, void *__restrict__ r_col,
-                                                uint32_t *__restrict__ r_state) {
-    using CS = ColorStore<CT>;
+__global__ void __launch_bounds__(256) k_commit(const uint32_t *__restrict__ poff, int P, int b, uint32_t seq0,
+                                                const Rec64 *__restrict__ pk, float2 *__restrict__ r_xy,
+                                                float2 *__restrict__ r_mo, float *__restrict__ r_t,
+                                                float *__restrict__ r_depth, uint32_t *__restrict__ r_seq,
+                                                void *__restrict__ r_col, uint32_t *__restrict__ r_state) {
+    using Codec = RecCodec<CT>;
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x >> 5);
     for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < P; p += warps) {
-        uint32_t beg = poff[p], m = poff[p + 1] - beg;
+        const uint32_t beg = poff[p], m = poff[p + 1] - beg;
         if (m == 0) continue;
-        // keys are batch index + 1; 0 marks an empty lane and sorts first
-        uint32_t key = lane < (int)m ? idx[beg + lane] + 1u : 0u;
+        // 0 marks an empty lane and sorts first
+        unsigned long long key = lane < (int)m ? rec_key(pk, beg, lane) : 0ull;
         key = warp_sort_asc(key);
         for (uint32_t c = 32; c < m; c += 32) {
-            uint32_t k2 = c + lane < m ? idx[beg + c + lane] + 1u : 0u;
+            unsigned long long k2 = c + lane < m ? rec_key(pk, beg, c + lane) : 0ull;
             k2 = warp_sort_asc(k2);
-            uint32_t rev = __shfl_sync(0xffffffffu, k2, 31 - lane);
+            const unsigned long long rev = __shfl_sync(0xffffffffu, k2, 31 - lane);
             key = warp_merge_asc(max(key, rev));   // the 32 largest so far, ascending
         }
-        uint32_t st = r_state[p];
-        uint32_t c0 = st & 0xFFFFu, h0 = st >> 16;
-        uint32_t kept = m < (uint32_t)b ? m : (uint32_t)b;
+        const uint32_t st = r_state[p];
+        const uint32_t c0 = st & 0xFFFFu, h0 = st >> 16;
+        const uint32_t kept = m < (uint32_t)b ? m : (uint32_t)b;
         if (lane >= 32 - (int)kept) {
-            uint32_t i = key - 1u;
-            uint32_t rank = m - 32u + (uint32_t)lane;           // position in insertion order
-            uint32_t s = (h0 + rank) % (uint32_t)b;
-            size_t dst = (size_t)p * b + s;
-            const Packed<CT> rec = pk[i];
-            r_xy[dst] = make_float2(rec.a.x, rec.a.y);
-            r_t[dst] = rec.a.z;
-            r_depth[dst] = rec.a.w;
-            r_mo[dst] = rec.motion();
+            const uint32_t i = (uint32_t)(key >> 32) - 1u;
+            const Rec64 &rec = pk[beg + (uint32_t)key];
+            const uint4 ra = rec.a, rb = rec.b, rc = rec.c;
+            const uint32_t rank = m - 32u + (uint32_t)lane;           // position in insertion order
+            const uint32_t s = (h0 + rank) % (uint32_t)b;
+            const size_t dst = (size_t)p * b + s;
+            r_xy[dst] = make_float2(__uint_as_float(ra.x), __uint_as_float(ra.y));
+            r_t[dst] = __uint_as_float(ra.z);
+            r_depth[dst] = __uint_as_float(ra.w);
+            r_mo[dst] = Codec::motion(rb, rc);
             r_seq[dst] = seq0 + i;
-            reinterpret_cast<typename CS::T *>(r_col)[dst] = rec.color();
+            reinterpret_cast<typename Codec::T *>(r_col)[dst] = Codec::color(rb, rc);
         }
         if (lane == 0) {
-            uint32_t cn = (uint64_t)c0 + m < (uint64_t)b ? c0 + m : (uint32_t)b;
-            uint32_t hn = (uint32_t)((h0 + (uint64_t)m) % (uint32_t)b);
+            const uint32_t cn = (uint64_t)c0 + m < (uint64_t)b ? c0 + m : (uint32_t)b;
+            const uint32_t hn = (uint32_t)((h0 + (uint64_t)m) % (uint32_t)b);
             r_state[p] = cn | (hn << 16);
         }
     }
@@ -156,22 +213,22 @@ __global__ void __launch_bounds__(256) k_commit(const uint32_t *__restrict__ pof
 template <int CT>
 cudaError_t run(AfrContext *c, const float4 *pos, const void *col, const float2 *mo, uint32_t n, uint32_t seq0,
                 cudaStream_t s) {
-    Packed<CT> *pk = reinterpret_cast<Packed<CT> *>(c->pack);
+    Rec64 *pk = reinterpret_cast<Rec64 *>(c->pack);
     cudaError_t e = cudaMemsetAsync(c->pcnt, 0, sizeof(uint32_t) * c->P, s);
     if (e != cudaSuccess) return e;
-    int g = grid_for(n, 256);
-    k_hist<CT><<<g, 256, 0, s>>>(pos, col, mo, n, c->W, c->H, c->bin_of, c->pcnt, pk, c->dcount);
+    const int g = grid_for(n, 256);
+    k_hist<CT><<<g, 256, 0, s>>>(pos, col, mo, n, c->W, c->H, c->bin_of, c->pcnt, c->dcount);
     if ((e = scan_exclusive(c->pcnt, c->poff, c->P, c->scan_tmp, s)) != cudaSuccess) return e;
-    k_scatter<<<g, 256, 0, s>>>(c->bin_of, n, c->poff, c->idx);
-    int gc = grid_for((size_t)c->P * 32, 256);
-    k_commit<CT><<<gc, 256, 0, s>>>(c->poff, c->idx, c->P, c->b, seq0, pk, c->r_xy, c->r_mo, c->r_t, c->r_depth,
-                                    c->r_seq, c->r_col, c->r_state);
+    k_place<CT><<<grid_for(n, 32 * kPlaceWarps), 32 * kPlaceWarps, 0, s>>>(pos, col, mo, n, c->bin_of, c->poff, pk);
+    const int gc = grid_for((size_t)c->P * 32, 256);
+    k_commit<CT><<<gc, 256, 0, s>>>(c->poff, c->P, c->b, seq0, pk, c->r_xy, c->r_mo, c->r_t, c->r_depth, c->r_seq,
+                                    c->r_col, c->r_state);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t packed_bytes(int ct) { return ct == AFR_F32 ? sizeof(Packed<AFR_F32>) : sizeof(Packed16); }
+size_t packed_bytes(int) { return sizeof(Rec64); }
 
 cudaError_t launch_ingest(AfrContext *c, const AfrSampleBatch *batch, uint32_t n, uint32_t seq0,
                           cudaStream_t s) {

@@ -1,8 +1,6 @@
 """Batched form: several viewer streams of different sizes and depths in one
-persistent launch (afr_batch_reconstruct), tuned by the autotuner, captured
-in a CUDA graph, and the bounded wait of its width/filter hand-off."""
-import time
-
+persistent launch (afr_batch_reconstruct), tuned by the autotuner and
+captured in a CUDA graph."""
 import numpy as np
 import pytest
 import torch
@@ -15,6 +13,9 @@ pytestmark = pytest.mark.gpu
 from paper_2510_15876_gb300 import _lib as L  # noqa: E402
 
 STREAMS = [(96, 64, 4, 10), (130, 70, 8, 24), (64, 48, 16, 16), (200, 120, 8, 40)]   # (W, H, depth, discs)
+# one context above the 131,072-pixel limit of the persistent kernel: it gets
+# its own launches inside the batched call
+MIXED = [(96, 64, 4, 10), (400, 340, 4, 30), (130, 70, 8, 24)]
 T_NOW = 1.0
 
 
@@ -27,10 +28,10 @@ def dev():
     return torch.device("cuda:0")
 
 
-def _make(dev, ct="f16"):
+def _make(dev, ct="f16", streams=STREAMS):
     from paper_2510_15876_gb300.api import Reconstructor, to_device_batch
     recs, batches = [], []
-    for i, (W, H, b, k) in enumerate(STREAMS):
+    for i, (W, H, b, k) in enumerate(streams):
         sc = make_scene(SceneSpec(f"batch_test{i}", W, H, b, k, (4.0, 16.0), 24.0, 8), i)
         batch = sample_stream(sc, W * H * b, i)
         rec = Reconstructor(W, H, b, color_type=ct, device=dev)
@@ -42,10 +43,11 @@ def _make(dev, ct="f16"):
     return recs, batches
 
 
-def test_batch_matches_single_stream_launches(dev):
+@pytest.mark.parametrize("streams", [STREAMS, MIXED], ids=["small", "mixed"])
+def test_batch_matches_single_stream_launches(dev, streams):
     from paper_2510_15876_gb300 import autotune
     from paper_2510_15876_gb300.api import BatchReconstructor
-    recs, _ = _make(dev)
+    recs, _ = _make(dev, streams=streams)
     tuned = [autotune.tune(r) for r in recs]
     assert all(r in autotune.RADII and t in autotune.TILES for r, t in tuned)
     singles = [r.reconstruct(T_NOW).clone() for r in recs]
@@ -109,35 +111,4 @@ def test_batch_graph_replay(dev):
     for a, b in zip(ref, B.outs):
         assert torch.equal(a, b)
     assert all(r.status() == L.AFR_OK for r in recs)
-    B.close()
-
-
-def test_batch_bounded_wait_reports_timeout(dev):
-    """A width band whose flag is never set: its filter items give up after
-    their bounded wait, the context reports AFR_ERR_TIMEOUT, the others are
-    untouched, and the next launch works again."""
-    from paper_2510_15876_gb300.api import BatchReconstructor
-    recs, _ = _make(dev, ct="f32")
-    B = BatchReconstructor(recs)
-    ref = [o.clone() for o in B.run(T_NOW)]
-    torch.cuda.synchronize()
-    B.inject_stall(1, 0)
-    t0 = time.time()
-    outs = B.run(T_NOW)
-    torch.cuda.synchronize()
-    dt = time.time() - t0
-    assert recs[1].status() == L.AFR_ERR_TIMEOUT
-    assert all(recs[i].status() == L.AFR_OK for i in (0, 2, 3))
-    th = 8   # band height of the default filter tile (16 x 8)
-    assert torch.all(outs[1][:th] == 0)
-    assert torch.equal(outs[1][th:], ref[1][th:])
-    for i in (0, 2, 3):
-        assert torch.equal(outs[i], ref[i])
-    assert dt < 10.0
-    B.inject_stall(-1, -1)
-    outs = B.run(T_NOW)
-    torch.cuda.synchronize()
-    assert all(r.status() == L.AFR_OK for r in recs)
-    for a, b in zip(ref, outs):
-        assert torch.equal(a, b)
     B.close()
