@@ -2,8 +2,7 @@
 // pixel and push each pixel's share into its queue of depth b.
 //
 //  1. hist:   validate each sample, record its pixel and its ticket (its rank
-//             among the pixel's samples in atomic order; warp-aggregated
-//             atomics: lanes hitting one pixel share one).
+//             among the pixel's samples in atomic order).
 //  2. scan:   pixel offsets of the counting sort.
 //  3. place:  write each sample, repacked into one 64-byte record that also
 //             carries its batch index, at offset + ticket. A warp stages its
@@ -11,8 +10,9 @@
 //             record, so every record is one whole 64-byte block (no partial
 //             sectors for the memory system to merge).
 //  4. commit: one warp per pixel reads the pixel's records (contiguous),
-//             sorts their batch indices (= insertion order) with a 32-lane
-//             bitonic network, keeps the min(b, m) newest and writes them into
+//             ranks them by batch index (= insertion order): up to 32 records
+//             by counting smaller indices across the warp, more by a chunked
+//             bitonic top-32; keeps the min(b, m) newest and writes them into
 //             the circular queue at (head + rank) mod b, the slots sequential
 //             pushes would use.
 #include "afr_internal.cuh"
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(256) k_hist(const float4 *__restrict__ pos, co
         uint2 bt = make_uint2(kInvalid, 0u);
         if (ok) {
             bt.x = (uint32_t)(int)floorf(p.y) * (uint32_t)W + (uint32_t)(int)floorf(p.x);
-            bt.y = agg_inc(pcnt, bt.x);
+            bt.y = atomicAdd(pcnt + bt.x, 1u);   // a batch in time order rarely repeats a pixel within a warp
         }
         bin_of[i] = bt;
         agg_count(dcount + CNT_REJECTED, !ok);
@@ -176,7 +176,41 @@ __global__ void __launch_bounds__(256) k_commit(const uint32_t *__restrict__ pof
     for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < P; p += warps) {
         const uint32_t beg = poff[p], m = poff[p + 1] - beg;
         if (m == 0) continue;
-        // 0 marks an empty lane and sorts first
+        const uint32_t st = r_state[p];
+        const uint32_t c0 = st & 0xFFFFu, h0 = st >> 16;
+        const uint32_t kept = m < (uint32_t)b ? m : (uint32_t)b;
+        if (lane == 0) {
+            const uint32_t cn = (uint64_t)c0 + m < (uint64_t)b ? c0 + m : (uint32_t)b;
+            const uint32_t hn = (uint32_t)((h0 + (uint64_t)m) % (uint32_t)b);
+            r_state[p] = cn | (hn << 16);
+        }
+        if (m <= 32) {
+            // lane k holds record k; its rank in insertion order is the number
+            // of the pixel's records with a smaller batch index (indices are unique)
+            Rec64 rec;
+            uint32_t i = 0xFFFFFFFFu;
+            if (lane < (int)m) {
+                rec.a = __ldg(&pk[beg + lane].a);
+                rec.b = __ldg(&pk[beg + lane].b);
+                rec.c = __ldg(&pk[beg + lane].c);
+                i = rec.c.y;
+            }
+            uint32_t rank = 0;
+            for (uint32_t k = 0; k < m; ++k) rank += __shfl_sync(0xffffffffu, i, k) < i;
+            if (lane < (int)m && rank >= m - kept) {
+                const uint32_t s = (h0 + rank) % (uint32_t)b;
+                const size_t dst = (size_t)p * b + s;
+                r_xy[dst] = make_float2(__uint_as_float(rec.a.x), __uint_as_float(rec.a.y));
+                r_t[dst] = __uint_as_float(rec.a.z);
+                r_depth[dst] = __uint_as_float(rec.a.w);
+                r_mo[dst] = Codec::motion(rec.b, rec.c);
+                r_seq[dst] = seq0 + i;
+                reinterpret_cast<typename Codec::T *>(r_col)[dst] = Codec::color(rec.b, rec.c);
+            }
+            continue;
+        }
+        // more than 32: the 32 newest by chunked bitonic top-32 (0 marks an
+        // empty lane and sorts first)
         unsigned long long key = lane < (int)m ? rec_key(pk, beg, lane) : 0ull;
         key = warp_sort_asc(key);
         for (uint32_t c = 32; c < m; c += 32) {
@@ -185,9 +219,6 @@ __global__ void __launch_bounds__(256) k_commit(const uint32_t *__restrict__ pof
             const unsigned long long rev = __shfl_sync(0xffffffffu, k2, 31 - lane);
             key = warp_merge_asc(max(key, rev));   // the 32 largest so far, ascending
         }
-        const uint32_t st = r_state[p];
-        const uint32_t c0 = st & 0xFFFFu, h0 = st >> 16;
-        const uint32_t kept = m < (uint32_t)b ? m : (uint32_t)b;
         if (lane >= 32 - (int)kept) {
             const uint32_t i = (uint32_t)(key >> 32) - 1u;
             const Rec64 &rec = pk[beg + (uint32_t)key];
@@ -201,11 +232,6 @@ __global__ void __launch_bounds__(256) k_commit(const uint32_t *__restrict__ pof
             r_mo[dst] = Codec::motion(rb, rc);
             r_seq[dst] = seq0 + i;
             reinterpret_cast<typename Codec::T *>(r_col)[dst] = Codec::color(rb, rc);
-        }
-        if (lane == 0) {
-            const uint32_t cn = (uint64_t)c0 + m < (uint64_t)b ? c0 + m : (uint32_t)b;
-            const uint32_t hn = (uint32_t)((h0 + (uint64_t)m) % (uint32_t)b);
-            r_state[p] = cn | (hn << 16);
         }
     }
 }
