@@ -40,6 +40,10 @@ T_NOW = 1.0
 # launch sequences in csrc/ issue them
 LAUNCHES = {"ingest": 6, "gradients": 2, "reproject": 7, "reconstruct": 2, "feedback": 1}
 STAGES = ["ingest", "gradients", "reproject", "reconstruct", "feedback"]
+# DRAM bytes (read + write) of one k_filter launch, from an ncu capture of the
+# current filter kernel on this workload (profiles/k_filter_c2_1024x1024x8_and_c3_dram.md);
+# a changed kernel needs a new capture before a value is reported here.
+FILTER_TRAFFIC = {("c3_1920x1080x16", "f32"): 988529920 + 34030592}
 
 
 def _peaks():
@@ -250,7 +254,8 @@ def run_ours(args, rank, world):
     ach = flops / (r0["filter_ms"] * 1e-3) / 1e12
     roof = {"bound": "alu", "kernel": "k_filter", "kernel_ms": round(r0["filter_ms"], 4), "achieved": round(ach, 2),
             "peak": round(fp32_peak, 1), "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
-            "traffic": args.filter_traffic,
+            "traffic": args.filter_traffic if args.filter_traffic is not None
+            else FILTER_TRAFFIC.get((args.workload, forms[0])),
             "peak_source": "FP32 issue peak: 152 SMs x 128 lanes x 2 FLOP (FMA) x 2.07 GHz",
             "work": f"{pairs} sample-pixel pairs x 16 FLOP"}
     stage_hbm = {s: round(by[s] / (st[s] * 1e-3) / 1e9 / hbm_peak, 4) for s in STAGES}
