@@ -141,6 +141,14 @@ def pairs_of(off, W, H, R):
     return tot
 
 
+def arm_config(workload, n, seed, world):
+    """The workload description both arms print."""
+    return {"workload": f"{workload} (1920x1080 image, 16-deep buffer, {n} samples per batch, 256 moving discs, "
+                        f"10% occlusion-edge pixels, seed {seed})",
+            "global_batch": n * world, "l2": "inputs larger than L2 (1.3 GB batch), no flush",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
 # ------------------------------------------------------------------------------ our arm
 def run_ours(args, rank, world):
     import torch
@@ -326,10 +334,7 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": round(value, 3), "unit": "reconstructions/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{args.workload} (1920x1080 image, 16-deep buffer, {n} samples per batch, 256 "
-                               f"moving discs, 10% occlusion-edge pixels, seed {seed})",
-                   "global_batch": n * world, "l2": "inputs larger than L2 (1.3 GB batch), no flush",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "config": arm_config(args.workload, n, seed, world),
         "mpixel_per_s": round(P * value / 1e6, 1),
         "samples_filtered_per_s": round(frame * value, 0),
         "pairs_per_step": pairs,
@@ -536,7 +541,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "reconstructions/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per_image * 1e3, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD} (1920x1080 image, 16-deep buffer)", "parallelism": "single host thread"},
+        "config": arm_config(WORKLOAD, batch["pos"].shape[0], 0, 1),
         "cpu_baseline": {"value": round(value, 6), "unit": "reconstructions/s", "cores": 1, "kind": "oracle",
                          "sample": f"each step: the whole oracle path on a 1920x{band} band, scaled by {H}/{band}"},
         "e2e": {"value": round(value, 6), "unit": "reconstructions/s", "h2d_bytes_per_step": 0,
