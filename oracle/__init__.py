@@ -17,6 +17,10 @@ Parity status of each function (what pins it, in tests/test_oracle_pins.py):
 * filter      -- pinned: constant colour, partition of unity, one- and
                  two-sample closed forms, brute force, a numpy scatter sum.
 * backward    -- pinned: central finite differences of the oracle's forward.
+* coverage    -- pinned: hand-computed updates (growth, shrinkage, clamps,
+                 border means), a numpy count of records per disc, hole
+                 filling, and the per-pixel-radius filter against brute force
+                 and against the fixed-radius filter.
 """
 from __future__ import annotations
 
@@ -73,6 +77,14 @@ def lib():
             L.afo_filter.argtypes = [i32, i32, i32, P, P, f32, P, P, P, i64, P]
             L.afo_filter_brute.restype = None
             L.afo_filter_brute.argtypes = [i32, i32, i32, i64, P, f32, P, P, P]
+            L.afo_coverage_update.restype = None
+            L.afo_coverage_update.argtypes = [i32, i32, P, P, f32, f32, P, P]
+            L.afo_coverage_count.restype = None
+            L.afo_coverage_count.argtypes = [i32, i32, P, P, P]
+            L.afo_filter_var.restype = None
+            L.afo_filter_var.argtypes = [i32, i32, P, P, P, f32, P, P, P, i64, P]
+            L.afo_filter_brute_var.restype = None
+            L.afo_filter_brute_var.argtypes = [i32, i32, P, i64, P, f32, P, P, P]
             L.afo_backward.restype = None
             L.afo_backward.argtypes = [i32, i32, i32, i32, i32, P, P, P, P, P, f64, f64,
                                        P, P, f32, P, P, P]
@@ -157,13 +169,21 @@ def sigma(ring_count, W, H, grads, theta=DEFAULT_THETA, S: int = 32, window: flo
     return ss, st
 
 
-def filter_image(W, H, off, rec, sig_s, sig_t, R: int = 4, t_now: float = 1.0, pixels=None):
+def filter_image(W, H, off, rec, sig_s, sig_t, R=4, t_now: float = 1.0, pixels=None):
+    """R: one disc radius, or an array of W*H per-pixel radii."""
     out = np.zeros((W * H, 4))
     rec = np.ascontiguousarray(rec, np.float32)
     if rec.size == 0:
         rec = np.zeros((1, NR), np.float32)
     ss = np.ascontiguousarray(sig_s, np.float64)
     st = np.ascontiguousarray(sig_t, np.float64)
+    if not np.isscalar(R):
+        Rp = np.ascontiguousarray(R, np.int32).reshape(-1)
+        assert Rp.size == W * H
+        px = None if pixels is None else np.ascontiguousarray(pixels, np.int64)
+        lib().afo_filter_var(W, H, _p(Rp), _p(off), _p(rec), t_now, _p(ss), _p(st),
+                             None if px is None else _p(px), 0 if px is None else px.size, _p(out))
+        return out
     if pixels is None:
         lib().afo_filter(W, H, R, _p(off), _p(rec), t_now, _p(ss), _p(st), None, 0, _p(out))
     else:
@@ -173,12 +193,19 @@ def filter_image(W, H, off, rec, sig_s, sig_t, R: int = 4, t_now: float = 1.0, p
     return out
 
 
-def filter_brute(W, H, rec, sig_s, sig_t, R: int = 4, t_now: float = 1.0):
+def filter_brute(W, H, rec, sig_s, sig_t, R=4, t_now: float = 1.0):
+    """R: one disc radius, or an array of W*H per-pixel radii."""
     out = np.zeros((W * H, 4))
     rec = np.ascontiguousarray(rec, np.float32)
     n = rec.shape[0]
     if n == 0:
         rec = np.zeros((1, NR), np.float32)
+    if not np.isscalar(R):
+        Rp = np.ascontiguousarray(R, np.int32).reshape(-1)
+        lib().afo_filter_brute_var(W, H, _p(Rp), n, _p(rec), t_now,
+                                   _p(np.ascontiguousarray(sig_s, np.float64)),
+                                   _p(np.ascontiguousarray(sig_t, np.float64)), _p(out))
+        return out
     lib().afo_filter_brute(W, H, R, n, _p(rec), t_now,
                            _p(np.ascontiguousarray(sig_s, np.float64)),
                            _p(np.ascontiguousarray(sig_t, np.float64)), _p(out))
@@ -199,6 +226,40 @@ def backward(ring_count, W, H, grads, off, rec, grad_rgb, theta=DEFAULT_THETA, S
                        _p(rec), t_now, _p(np.ascontiguousarray(grad_rgb, np.float64)),
                        _p(gcol), _p(gth))
     return gcol[:n], gth
+
+
+def coverage_update(W, H, r_prev, n_prev, r_min: float = 0.5, r_max: float = 8.0):
+    """Next footprint radii (float32 r, integer R) from the previous image's
+    radii and sample counts (n_prev < 0: no information)."""
+    rp = np.ascontiguousarray(r_prev, np.float32).reshape(-1)
+    npv = np.ascontiguousarray(n_prev, np.int32).reshape(-1)
+    r_next = np.zeros(W * H, np.float32)
+    R_next = np.zeros(W * H, np.int32)
+    lib().afo_coverage_update(W, H, _p(rp), _p(npv), r_min, r_max, _p(r_next), _p(R_next))
+    return r_next, R_next
+
+
+def coverage_count(W, H, Rp, off):
+    n = np.zeros(W * H, np.int32)
+    lib().afo_coverage_count(W, H, _p(np.ascontiguousarray(Rp, np.int32).reshape(-1)),
+                             _p(np.ascontiguousarray(off, np.uint32)), _p(n))
+    return n
+
+
+def reconstruct_adaptive(ring: Ring, state: dict, t_now: float = 1.0, theta=DEFAULT_THETA, S: int = 32,
+                         window: float = 1.0, eps: float = 1e-4, r_min: float = 0.5, r_max: float = 8.0,
+                         pixels=None):
+    """One image with footprints sized by the coverage of the previous one
+    (section 6.2). state holds 'r' (float32 radii used last time) and 'n'
+    (samples that reached each pixel, -1 if unknown); it is updated."""
+    W, H = ring.W, ring.H
+    grads = gradients(ring, t_now)
+    off, rec, rseq, dropped = reproject(ring, t_now)
+    ss, st = sigma(ring.count, W, H, grads, theta, S, window, eps)
+    r, Rp = coverage_update(W, H, state["r"], state["n"], r_min, r_max)
+    img = filter_image(W, H, off, rec, ss, st, Rp, t_now, pixels)
+    state["r"], state["n"] = r, coverage_count(W, H, Rp, off)
+    return {"off": off, "rec": rec, "sig_s": ss, "sig_t": st, "R": Rp, "image": img}
 
 
 def reconstruct(ring: Ring, t_now: float = 1.0, theta=DEFAULT_THETA, S: int = 32, R: int = 4,

@@ -441,6 +441,97 @@ void afo_filter_brute(int W, int H, int R, int64_t n, const float *rec, float t_
 }
 
 /* ------------------------------------------------------------------------ */
+/* Section 6.2: splat sizes follow the previous image's coverage map. A region
+ * keeps the mean size used there, grows it fourfold where a pixel received
+ * fewer than 4 samples and shrinks it by 0.7 where more than 32 reached it. */
+void afo_coverage_update(int W, int H, const float *r_prev, const int32_t *n_prev,
+                         float r_min, float r_max, float *r_next, int32_t *R_next)
+{
+    for (int j = 0; j < H; ++j)
+        for (int i = 0; i < W; ++i) {
+            float sum = 0.0f;
+            int cnt = 0;
+            for (int dj = -1; dj <= 1; ++dj)
+                for (int di = -1; di <= 1; ++di) {
+                    int qi = i + di, qj = j + dj;
+                    if (qi < 0 || qj < 0 || qi >= W || qj >= H) continue;
+                    sum = sum + r_prev[(size_t)qj * W + qi];
+                    ++cnt;
+                }
+            size_t p = (size_t)j * W + i;
+            float mean = sum / (float)cnt;
+            int32_t n = n_prev[p];
+            float f = n < 0 ? 1.0f : n < 4 ? 4.0f : n > 32 ? 0.7f : 1.0f;
+            float r = mean * f;
+            if (r < r_min) r = r_min;
+            if (r > r_max) r = r_max;
+            r_next[p] = r;
+            R_next[p] = (int32_t)floorf(r + 0.5f);
+        }
+}
+
+void afo_coverage_count(int W, int H, const int32_t *Rp, const uint32_t *off, int32_t *n)
+{
+    for (int j = 0; j < H; ++j)
+        for (int i = 0; i < W; ++i) {
+            int R = Rp[(size_t)j * W + i];
+            int64_t c = 0;
+            for (int dj = -R; dj <= R; ++dj)
+                for (int di = -R; di <= R; ++di) {
+                    int qi = i + di, qj = j + dj;
+                    if (di * di + dj * dj > R * R || qi < 0 || qj < 0 || qi >= W || qj >= H) continue;
+                    size_t q = (size_t)qj * W + qi;
+                    c += off[q + 1] - off[q];
+                }
+            n[(size_t)j * W + i] = (int32_t)c;
+        }
+}
+
+void afo_filter_var(int W, int H, const int32_t *Rp, const uint32_t *off, const float *rec,
+                    float t_now, const double *sig_s, const double *sig_t,
+                    const int64_t *pixels, int64_t n_pixels, double *out)
+{
+    if (pixels) {
+        for (int64_t k = 0; k < n_pixels; ++k) {
+            int64_t p = pixels[k];
+            filter_pixel(W, H, Rp[p], off, rec, t_now, sig_s[p], sig_t[p], (int)(p % W),
+                         (int)(p / W), out + p * 4);
+        }
+        return;
+    }
+    for (int j = 0; j < H; ++j)
+        for (int i = 0; i < W; ++i) {
+            size_t p = (size_t)j * W + i;
+            filter_pixel(W, H, Rp[p], off, rec, t_now, sig_s[p], sig_t[p], i, j, out + p * 4);
+        }
+}
+
+void afo_filter_brute_var(int W, int H, const int32_t *Rp, int64_t n, const float *rec,
+                          float t_now, const double *sig_s, const double *sig_t, double *out)
+{
+    for (int j = 0; j < H; ++j)
+        for (int i = 0; i < W; ++i) {
+            size_t p = (size_t)j * W + i;
+            int R = Rp[p];
+            double cx = i + 0.5, cy = j + 0.5, acc[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int64_t e = 0; e < n; ++e) {
+                const float *r = rec + (size_t)e * AFO_NR;
+                int qi = (int)floorf(r[AFO_RX]), qj = (int)floorf(r[AFO_RY]);
+                if ((qi - i) * (qi - i) + (qj - j) * (qj - j) > R * R) continue;
+                double dx = (double)r[AFO_RX] - cx, dy = (double)r[AFO_RY] - cy;
+                double a = (double)t_now - (double)r[AFO_RT];
+                double w = gauss_weight(dx * dx + dy * dy, a, sig_s[p], sig_t[p]);
+                acc[0] += w * r[AFO_RR];
+                acc[1] += w * r[AFO_RG];
+                acc[2] += w * r[AFO_RB];
+                acc[3] += w;
+            }
+            for (int c = 0; c < 3; ++c) out[p * 4 + c] = acc[3] > 0.0 ? acc[c] / acc[3] : 0.0;
+            out[p * 4 + 3] = acc[3];
+        }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Adjoint. C_p = sum_s w_ps c_s / W_p, so dC_p/dc_s = w_ps / W_p. A width
  * sigma moves every weight of the pixel: dw/dsigma_s = w d^2 / sigma_s^3 and
  * dw/dsigma_t = w a^2 / sigma_t^3, so dC_p/dsigma = (sum dw c - C_p sum dw) / W_p.

@@ -75,6 +75,26 @@ void afo_filter(int W, int H, int R, const uint32_t *off, const float *rec,
 void afo_filter_brute(int W, int H, int R, int64_t n, const float *rec, float t_now,
                       const double *sig_s, const double *sig_t, double *out);
 
+/* Section 6.2, coverage map, in gather form: the footprint radius of each
+ * pixel for the next image is the mean of the radii used for the previous
+ * image over the pixel's 3x3 neighbourhood (clipped at the border), times 4
+ * where fewer than 4 samples reached the pixel, times 0.7 where more than 32
+ * did (n_prev < 0: no information, times 1), clamped to [r_min, r_max]; the
+ * integer disc radius is floor(r + 1/2). Single precision, one rounding per
+ * operation: the result decides an integer. */
+void afo_coverage_update(int W, int H, const float *r_prev, const int32_t *n_prev,
+                         float r_min, float r_max, float *r_next, int32_t *R_next);
+
+/* Number of frame-view records in each pixel's integer disc of radius Rp[p]. */
+void afo_coverage_count(int W, int H, const int32_t *Rp, const uint32_t *off, int32_t *n);
+
+/* afo_filter and afo_filter_brute with a per-pixel disc radius Rp. */
+void afo_filter_var(int W, int H, const int32_t *Rp, const uint32_t *off, const float *rec,
+                    float t_now, const double *sig_s, const double *sig_t,
+                    const int64_t *pixels, int64_t n_pixels, double *out);
+void afo_filter_brute_var(int W, int H, const int32_t *Rp, int64_t n, const float *rec,
+                          float t_now, const double *sig_s, const double *sig_t, double *out);
+
 /* Adjoint of the filter and the width mapping for a loss with per-pixel
  * gradient grad_rgb (3 doubles per pixel): gradient with respect to the
  * colours of the frame-view records (3 doubles per record) and to theta. */

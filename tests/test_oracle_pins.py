@@ -519,3 +519,99 @@ def test_backward_matches_central_differences():
             hh = float(np.float32(rec[e, 3 + ch] + 0.25)) - float(np.float32(rec[e, 3 + ch] - 0.25))
             fd = fd * 0.5 / hh
             assert abs(fd - gcol[e, ch]) <= 1e-7 * max(1.0, abs(fd))
+
+
+# ---- section 6.2: coverage-driven footprint sizes ------------------------------
+
+def test_coverage_update_hand_cases():
+    """Growth by 4 below 4 samples, shrinkage by 0.7 above 32, unchanged in
+    between and without information, clamps, and the rounding to a disc."""
+    W, H = 4, 1
+    r = np.full(W * H, 2.0, np.float32)
+    n = np.array([-1, 2, 10, 40], np.int32)
+    r_next, R_next = oracle.coverage_update(W, H, r, n)
+    assert r_next.tolist() == [2.0, 8.0, 2.0, float(np.float32(np.float32(2.0) * np.float32(0.7)))]
+    assert R_next.tolist() == [2, 8, 2, 1]
+    # boundaries: exactly 4 and exactly 32 samples change nothing
+    r_next, _ = oracle.coverage_update(2, 1, np.full(2, 3.0, np.float32), np.array([4, 32], np.int32))
+    assert r_next.tolist() == [3.0, 3.0]
+    # clamps: growth stops at r_max, shrinkage at r_min; r = 2.5 rounds up
+    r_next, R_next = oracle.coverage_update(3, 1, np.array([5.0, 5.0, 5.0], np.float32),
+                                            np.array([0, 100, 5], np.int32), r_min=0.5, r_max=8.0)
+    assert r_next.tolist()[0] == 8.0 and R_next[0] == 8
+    r_next, R_next = oracle.coverage_update(1, 1, np.array([0.6], np.float32), np.array([100], np.int32))
+    assert r_next[0] == np.float32(0.5) and R_next[0] == 1
+    _, R_next = oracle.coverage_update(1, 1, np.array([2.5], np.float32), np.array([10], np.int32))
+    assert R_next[0] == 3
+
+
+def test_coverage_update_region_mean_at_borders():
+    """The size is the mean over the pixel's 3x3 neighbourhood, clipped at the
+    border (a corner averages 4 pixels, an edge 6, the interior 9)."""
+    W, H = 3, 3
+    r = np.arange(1, 10, dtype=np.float32)            # 1..9 row-major
+    r_next, _ = oracle.coverage_update(W, H, r, np.full(9, 10, np.int32), r_max=100.0)
+    g = r.reshape(3, 3).astype(np.float64)
+    for j in range(3):
+        for i in range(3):
+            win = g[max(0, j - 1):j + 2, max(0, i - 1):i + 2]
+            assert abs(r_next[j * 3 + i] - win.mean()) < 1e-6
+    assert r_next[4] == np.float32(5.0)               # (1 + ... + 9) / 9
+
+
+def test_coverage_count_matches_numpy():
+    rng = np.random.default_rng(11)
+    W, H = 13, 9
+    off, rec = _random_frame(rng, W, H, 400)
+    Rp = rng.integers(0, 5, W * H).astype(np.int32)
+    n = oracle.coverage_count(W, H, Rp, off)
+    cnt = np.diff(off.astype(np.int64)).reshape(H, W)
+    for j in range(H):
+        for i in range(W):
+            R = Rp[j * W + i]
+            ref = sum(int(cnt[j + dj, i + di]) for dj in range(-R, R + 1) for di in range(-R, R + 1)
+                      if di * di + dj * dj <= R * R and 0 <= i + di < W and 0 <= j + dj < H)
+            assert n[j * W + i] == ref
+
+
+def test_per_pixel_radius_filter_equals_brute_force_and_fixed_radius():
+    rng = np.random.default_rng(12)
+    W, H = 12, 10
+    off, rec = _random_frame(rng, W, H, 450)
+    ss = rng.uniform(0.5, 3.0, W * H)
+    st = rng.uniform(0.05, 1.0, W * H)
+    Rp = rng.integers(0, 6, W * H).astype(np.int32)
+    out = oracle.filter_image(W, H, off, rec, ss, st, R=Rp)
+    brute = oracle.filter_brute(W, H, rec, ss, st, R=Rp)
+    np.testing.assert_allclose(out, brute, rtol=1e-12, atol=1e-300)
+    for R in (0, 3):
+        fixed = oracle.filter_image(W, H, off, rec, ss, st, R=R)
+        var = oracle.filter_image(W, H, off, rec, ss, st, R=np.full(W * H, R, np.int32))
+        np.testing.assert_array_equal(fixed, var)
+
+
+def test_coverage_fills_a_disocclusion_hole():
+    """A region without samples is a hole at a small footprint; the next
+    image grows the footprints there fourfold and fills it."""
+    rng = np.random.default_rng(13)
+    W, H, b = 24, 24, 4
+    n = W * H * b
+    pos = np.zeros((n, 4), np.float32)
+    pos[:, 0] = rng.uniform(0, W, n)
+    pos[:, 1] = rng.uniform(0, H, n)
+    pos[:, 2] = np.sort(rng.uniform(0, 1, n))
+    keep = (pos[:, 0] - 12) ** 2 + (pos[:, 1] - 12) ** 2 > 3.5 ** 2   # a hole of radius 3.5
+    pos = pos[keep]
+    col = np.zeros((len(pos), 4), np.float32)
+    col[:, :3] = 0.5
+    ring = oracle.Ring(W, H, b)
+    ring.insert(pos, col, np.zeros((len(pos), 2), np.float32))
+    state = {"r": np.full(W * H, 1.0, np.float32), "n": np.full(W * H, -1, np.int32)}
+    first = oracle.reconstruct_adaptive(ring, state)
+    holes = first["image"][:, 3] == 0
+    assert holes.sum() > 0 and (first["R"] == 1).all()
+    assert (state["n"][holes] < 4).all()
+    second = oracle.reconstruct_adaptive(ring, state)
+    assert (second["R"][holes] == 4).all()
+    assert (second["image"][:, 3] > 0).all()
+    np.testing.assert_allclose(second["image"][:, :3], 0.5, rtol=1e-12)
