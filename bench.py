@@ -268,6 +268,37 @@ def run_ours(args, rank, world):
             "work": f"{pairs} sample-pixel pairs x 16 FLOP"}
     stage_hbm = {s: round(by[s] / (st[s] * 1e-3) / 1e9 / hbm_peak, 4) for s in STAGES}
 
+    # adaptive footprints (section 6.2): successive reconstructions of the
+    # same frame view, each sizing footprints from the previous one's coverage
+    from paper_2510_15876_gb300 import _lib as L
+    adapt = {}
+    if not args.quick:
+        _, pos, col, mo, out, tiles = keep
+        step(rec, pos, col, mo, out, tiles)
+        flags = L.AFR_RECON_ADAPTIVE_SUPPORT
+        rec.reconstruct(T_NOW, out=out, flags=flags | L.AFR_RECON_COVERAGE_RESET)
+        for _ in range(5):
+            rec.reconstruct(T_NOW, out=out, flags=flags)
+        torch.cuda.synchronize()
+        s3, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s3.record()
+        for _ in range(args.steps):
+            rec.reconstruct(T_NOW, out=out, flags=flags)
+        e3.record()
+        torch.cuda.synchronize()
+        radius = np.floor(rec.export_map(L.AFR_MAP_FOOTPRINT) + 0.5).astype(int)
+        cov = rec.export_map(L.AFR_MAP_COVERAGE)
+        holes_fixed = int((rec.reconstruct(T_NOW)[..., 3] == 0).sum())
+        adapt = {"ms_per_reconstruct": round(s3.elapsed_time(e3) / args.steps, 4),
+                 "fixed_ms_per_reconstruct": round(st["reconstruct"], 4),
+                 "footprint_radius_counts": {str(k): int((radius == k).sum()) for k in np.unique(radius)},
+                 "median_samples_per_footprint": float(np.median(cov)),
+                 "holes_fixed_R4": holes_fixed,
+                 "what": "afr_reconstruct with AFR_RECON_ADAPTIVE_SUPPORT after 6 warm-up images (coverage converged)"}
+        rec.reconstruct(T_NOW, out=out, flags=flags)
+        torch.cuda.synchronize()
+        adapt["holes_adaptive"] = int((out[..., 3] == 0).sum())
+
     # end to end through the public API, batch in pinned host memory: every
     # step copies its inputs host -> device and its image device -> host inside
     # the timed region; step k+1's input copy (on a copy stream, into the other
@@ -349,6 +380,7 @@ def run_ours(args, rank, world):
                                  "stage_ms": {k: round(v, 4) for k, v in results[ct]["stage_ms"].items()}}
                             for ct in results},
         "fwd_bwd": fb,
+        "adaptive_footprint": adapt,
         "batched": batched,
         "e2e": {"value": round(world * 1000.0 / e2e_ms, 3), "unit": "reconstructions/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4),

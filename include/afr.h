@@ -222,7 +222,9 @@ AFR_API AfrStatus afr_export_frame(AfrContext *ctx, uint32_t *off_host, float *r
 typedef enum {
     AFR_MAP_LBAR = 0,   /* age-weighted mean luminance (NaN where empty) */
     AFR_MAP_GX = 1, AFR_MAP_GY = 2, AFR_MAP_GT = 3,
-    AFR_MAP_SIGMA_S = 4, AFR_MAP_SIGMA_T = 5
+    AFR_MAP_SIGMA_S = 4, AFR_MAP_SIGMA_T = 5,
+    AFR_MAP_FOOTPRINT = 6,  /* footprint radius r of the last adaptive reconstruction (export only) */
+    AFR_MAP_COVERAGE = 7    /* samples in each pixel's footprint in that reconstruction (export only) */
 } AfrMap;
 
 /* Copies one width*height float map out / in. Importing a gradient map
@@ -236,9 +238,21 @@ AFR_API AfrStatus afr_import_map(AfrContext *ctx, AfrMap which, const float *map
  * order, device memory), e.g. to differentiate with respect to them. */
 AFR_API AfrStatus afr_set_frame_colors(AfrContext *ctx, const float *rgb_dev, afr_stream_t stream);
 
-enum { AFR_RECON_KEEP_SIGMA = 1 };
-/* afr_reconstruct with flags: AFR_RECON_KEEP_SIGMA filters with the width
- * map already in the context (imported or from the previous call). */
+enum { AFR_RECON_KEEP_SIGMA = 1, AFR_RECON_ADAPTIVE_SUPPORT = 2, AFR_RECON_COVERAGE_RESET = 4 };
+/* afr_reconstruct with flags. AFR_RECON_KEEP_SIGMA filters with the width
+ * map already in the context (imported or from the previous call).
+ *
+ * AFR_RECON_ADAPTIVE_SUPPORT (section 6.2, the coverage map, in gather
+ * form): each pixel gets its own footprint, the integer disc of radius
+ * floor(r + 1/2), where r is the mean of the radii used in the previous
+ * adaptive reconstruction over the pixel's 3x3 neighbourhood, times 4 if
+ * fewer than 4 samples reached the pixel then, times 0.7 if more than 32 did,
+ * clamped to [0.5, 8] (single precision, one rounding per operation). The
+ * radii and counts persist in the context between calls; they start as
+ * r = the configured radius and "no count" (factor 1), and
+ * AFR_RECON_COVERAGE_RESET returns them to that state before the update.
+ * afr_reconstruct_backward and the batched form use the configured radius
+ * only: backward after an adaptive reconstruction returns AFR_ERR_BAD_STATE. */
 AFR_API AfrStatus afr_reconstruct_ex(AfrContext *ctx, float t_now, const AfrParams *params,
                              uint32_t flags, float *out_rgbw_dev, afr_stream_t stream);
 

@@ -19,7 +19,8 @@ STATUS_NAMES = ["AFR_OK", "AFR_ERR_INVALID_ARG", "AFR_ERR_BAD_STATE", "AFR_ERR_O
                 "AFR_ERR_TIMEOUT", "AFR_ERR_DEVICE_CHECK"]
 AFR_F32, AFR_F16, AFR_BF16 = 0, 1, 2
 AFR_MAP_LBAR, AFR_MAP_GX, AFR_MAP_GY, AFR_MAP_GT, AFR_MAP_SIGMA_S, AFR_MAP_SIGMA_T = range(6)
-AFR_RECON_KEEP_SIGMA = 1
+AFR_MAP_FOOTPRINT, AFR_MAP_COVERAGE = 6, 7
+AFR_RECON_KEEP_SIGMA, AFR_RECON_ADAPTIVE_SUPPORT, AFR_RECON_COVERAGE_RESET = 1, 2, 4
 AFR_PROFILE_MAX_LAUNCHES = 256
 
 EXPORTED = [

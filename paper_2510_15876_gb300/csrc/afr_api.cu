@@ -35,7 +35,7 @@ cudaError_t dalloc(T **p, size_t n) {
 void free_all(AfrContext *c) {
     void *ptrs[] = {c->r_xy, c->r_mo, c->r_t, c->r_depth, c->r_seq, c->r_col, c->r_state, c->bin_of,
                     c->pack,
-                    c->pcnt, c->poff, c->lbar, c->grad, c->pstat, c->sigma, c->fconst, c->amin2, c->tiles, c->fcnt,
+                    c->pcnt, c->poff, c->lbar, c->grad, c->pstat, c->sigma, c->fconst, c->cov_r[0], c->cov_r[1], c->cov_n, c->amin2, c->tiles, c->fcnt,
                     c->foff, c->fpos, c->fcol, c->fseq, c->scan_tmp, c->bgrad, c->bparam, c->dcount, c->derr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -156,6 +156,9 @@ AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
     AFR_ALLOC(c->pstat, P);
     AFR_ALLOC(c->sigma, P);
     AFR_ALLOC(c->fconst, P);
+    AFR_ALLOC(c->cov_r[0], P);
+    AFR_ALLOC(c->cov_r[1], P);
+    AFR_ALLOC(c->cov_n, P);
     AFR_ALLOC(c->amin2, P);
     AFR_ALLOC(c->tiles, (size_t)c->ntiles);
     AFR_ALLOC(c->fcnt, P);
@@ -173,6 +176,8 @@ AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
     if (e == cudaSuccess) e = cudaMemset(c->foff, 0, (P + 1) * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(c->dcount, 0, afr::CNT_N * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->derr, 0, sizeof(uint32_t));
+    if (e == cudaSuccess) e = afr::launch_coverage_init(c, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         AfrStatus st = e == cudaErrorMemoryAllocation ? AFR_ERR_OOM : AFR_ERR_CUDA;
@@ -289,13 +294,17 @@ AfrStatus afr_reconstruct_ex(AfrContext *c, float t_now, const AfrParams *params
         return fail(c, AFR_ERR_INVALID_ARG, "afr_reconstruct: null or misaligned pointer");
     if (!params_ok(params)) return fail(c, AFR_ERR_INVALID_ARG, "afr_reconstruct: parameters not finite/positive");
     bool keep = (flags & AFR_RECON_KEEP_SIGMA) != 0;
+    const bool adaptive = (flags & AFR_RECON_ADAPTIVE_SUPPORT) != 0;
+    if (flags & ~(uint32_t)(AFR_RECON_KEEP_SIGMA | AFR_RECON_ADAPTIVE_SUPPORT | AFR_RECON_COVERAGE_RESET))
+        return fail(c, AFR_ERR_INVALID_ARG, "afr_reconstruct_ex: unknown flag");
     if (!c->frame_valid || c->frame_t != t_now)
         return fail(c, AFR_ERR_BAD_STATE, "afr_reconstruct: call afr_reproject for this t_now first");
     if (!keep && (!c->grads_valid || c->grads_t != t_now))
         return fail(c, AFR_ERR_BAD_STATE, "afr_reconstruct: call afr_estimate_gradients for this t_now first");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
-    e = afr::launch_sigma(c, params, keep, s);
+    if (flags & AFR_RECON_COVERAGE_RESET) e = afr::launch_coverage_init(c, s);
+    if (e == cudaSuccess) e = afr::launch_sigma(c, params, keep, adaptive, s);
     cudaEvent_t *pair = nullptr;
     if (e == cudaSuccess && c->prof_on && c->prof_n < AFR_PROFILE_MAX_LAUNCHES) {
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -304,7 +313,7 @@ AfrStatus afr_reconstruct_ex(AfrContext *c, float t_now, const AfrParams *params
         else if (e == cudaSuccess) pair = c->prof_ev + 2 * c->prof_n;
     }
     if (e == cudaSuccess && pair) e = cudaEventRecord(pair[0], s);
-    if (e == cudaSuccess) e = afr::launch_filter(c, t_now, reinterpret_cast<float4 *>(out_rgbw_dev), s);
+    if (e == cudaSuccess) e = afr::launch_filter(c, t_now, adaptive, reinterpret_cast<float4 *>(out_rgbw_dev), s);
     if (e == cudaSuccess && pair) {
         e = cudaEventRecord(pair[1], s);
         ++c->prof_n;
@@ -314,6 +323,7 @@ AfrStatus afr_reconstruct_ex(AfrContext *c, float t_now, const AfrParams *params
     c->recon_t = t_now;
     c->recon_params = *params;
     c->sigma_imported = keep;
+    c->adaptive_last = adaptive;
     return AFR_OK;
 }
 
@@ -338,6 +348,8 @@ AfrStatus afr_reconstruct_backward(AfrContext *c, const float *grad_rgb_dev, flo
         return fail(c, AFR_ERR_INVALID_ARG, "afr_reconstruct_backward: null or misaligned grad_rgb");
     if (!c->recon_valid || !c->frame_valid)
         return fail(c, AFR_ERR_BAD_STATE, "afr_reconstruct_backward: call afr_reconstruct first");
+    if (c->adaptive_last)
+        return fail(c, AFR_ERR_BAD_STATE, "afr_reconstruct_backward: not available after an adaptive reconstruction");
     if (grad_params_dev && (c->sigma_imported || !c->grads_valid))
         return fail(c, AFR_ERR_BAD_STATE,
                     "afr_reconstruct_backward: parameter gradients need widths computed from gradients");
@@ -467,6 +479,12 @@ AfrStatus afr_export_map(AfrContext *c, AfrMap which, float *map_host) {
     } else if (which == AFR_MAP_SIGMA_S || which == AFR_MAP_SIGMA_T) {
         e = cudaMemcpy2D(map_host, 4, reinterpret_cast<float *>(c->sigma) + (which - AFR_MAP_SIGMA_S), 8, 4, P,
                          cudaMemcpyDeviceToHost);
+    } else if (which == AFR_MAP_FOOTPRINT) {
+        e = cudaMemcpy(map_host, c->cov_r[c->cov_cur], P * 4, cudaMemcpyDeviceToHost);
+    } else if (which == AFR_MAP_COVERAGE) {
+        std::vector<int32_t> n(P);
+        e = cudaMemcpy(n.data(), c->cov_n, P * 4, cudaMemcpyDeviceToHost);
+        for (size_t p = 0; p < P && e == cudaSuccess; ++p) map_host[p] = (float)n[p];
     } else {
         return fail(c, AFR_ERR_INVALID_ARG, "afr_export_map: unknown map");
     }
@@ -672,8 +690,9 @@ AfrStatus afr_batch_reconstruct(AfrBatch *b, float t_now, const AfrParams *param
     cudaError_t e = cudaSuccess;
     for (int q = 0; q < b->n_direct && e == cudaSuccess; ++q) {
         AfrContext *c = b->ctxs[q];
-        e = afr::launch_sigma(c, params, false, s);
-        if (e == cudaSuccess) e = afr::launch_filter(c, t_now, reinterpret_cast<float4 *>(outs_dev[b->user_index[q]]), s);
+        e = afr::launch_sigma(c, params, false, false, s);
+        if (e == cudaSuccess)
+            e = afr::launch_filter(c, t_now, false, reinterpret_cast<float4 *>(outs_dev[b->user_index[q]]), s);
     }
     const int m = n - b->n_direct;
     if (m > 0) {
@@ -690,6 +709,7 @@ AfrStatus afr_batch_reconstruct(AfrBatch *b, float t_now, const AfrParams *param
         c->recon_t = t_now;
         c->recon_params = *params;
         c->sigma_imported = false;
+        c->adaptive_last = false;
     }
     return AFR_OK;
 }

@@ -85,7 +85,12 @@ struct AfrContext {
     float4 *grad = nullptr;       // [P] (Gx, Gy, Gt, Lbar)
     float4 *pstat = nullptr;      // [P] (sum w, mean L, M2, Gt)
     float2 *sigma = nullptr;      // [P] (sigma_s, sigma_t)
-    float4 *fconst = nullptr;     // [P] gather constants (-ks, -kt, exponent shift m, 0) of each pixel
+    float4 *fconst = nullptr;     // [P] gather constants (-ks, -kt, exponent shift m, disc radius as int bits)
+    float *cov_r[2] = {nullptr, nullptr};   // [P] footprint radii of adaptive reconstructions (ping-pong)
+    int32_t *cov_n = nullptr;     // [P] samples in each pixel's footprint in the last adaptive reconstruction
+    int cov_cur = 0;              // cov_r[cov_cur] holds the radii of the last adaptive reconstruction
+    bool cov_init = false;        // the coverage state holds its start values
+    bool adaptive_last = false;   // the last reconstruction used adaptive footprints
     uint32_t *amin2 = nullptr;    // [P] float bits of min a^2 per frame bin
     afr::TilePartial *tiles = nullptr;  // [ntiles]
 
@@ -213,8 +218,9 @@ cudaError_t launch_ingest(AfrContext *c, const AfrSampleBatch *batch, uint32_t n
                           cudaStream_t s);
 cudaError_t launch_gradients(AfrContext *c, float t_now, cudaStream_t s);
 cudaError_t launch_reproject(AfrContext *c, float t_now, cudaStream_t s);
-cudaError_t launch_sigma(AfrContext *c, const AfrParams *prm, bool keep, cudaStream_t s);
-cudaError_t launch_filter(AfrContext *c, float t_now, float4 *out, cudaStream_t s);
+cudaError_t launch_sigma(AfrContext *c, const AfrParams *prm, bool keep, bool adaptive, cudaStream_t s);
+cudaError_t launch_coverage_init(AfrContext *c, cudaStream_t s);
+cudaError_t launch_filter(AfrContext *c, float t_now, bool adaptive, float4 *out, cudaStream_t s);
 cudaError_t launch_feedback(AfrContext *c, AfrTileStats *out, cudaStream_t s);
 cudaError_t launch_backward(AfrContext *c, const float4 *grad_rgb, float *grad_col, float *grad_prm,
                             cudaStream_t s);

@@ -92,14 +92,17 @@ __device__ __forceinline__ float shifted_exponent(const PixelFrame &f, float4 r)
 }
 
 // Filter widths of every pixel (unless KEEP: the widths already in the map
-// are used) and the pixel's gather constants for the filter: -ks, -kt and the
-// exponent shift m.
-template <bool KEEP>
+// are used) and the pixel's gather constants for the filter: -ks, -kt, the
+// exponent shift m and the footprint radius (the configured R, or with ADAPT
+// floor(r + 1/2) of the pixel's adaptive radius r, whose sample count is then
+// recorded for the next update).
+template <bool KEEP, bool ADAPT>
 __global__ void __launch_bounds__(256) k_sigma(int W, int H, int R, int S, int ntx, float window, float eps,
                                                AfrParams prm, const float4 *__restrict__ grad,
                                                const TilePartial *__restrict__ tiles,
-                                               const uint32_t *__restrict__ amin2, float2 *__restrict__ sigma,
-                                               float4 *__restrict__ fconst) {
+                                               const uint32_t *__restrict__ amin2, const float *__restrict__ radius,
+                                               const uint32_t *__restrict__ foff, int32_t *__restrict__ cov_n,
+                                               float2 *__restrict__ sigma, float4 *__restrict__ fconst) {
     int P = W * H;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
         int x = p % W, y = p / W;
@@ -111,8 +114,58 @@ __global__ void __launch_bounds__(256) k_sigma(int W, int H, int R, int S, int n
             sg = make_float2(w.ss, w.st);
             sigma[p] = sg;
         }
-        PixelFrame f = pixel_frame(x, y, W, H, R, sg, amin2);
-        fconst[p] = make_float4(-f.ks, -f.kt, f.m, 0.f);
+        int Rp = R;
+        if (ADAPT) {
+            Rp = (int)floorf(__fadd_rn(__ldg(radius + p), 0.5f));
+            int32_t n = 0;
+            for (int dy = -Rp; dy <= Rp; ++dy) {
+                const int row = y + dy;
+                if (row < 0 || row >= H) continue;
+                const int hw = half_width(Rp, dy);
+                const int x0 = max(0, x - hw), x1 = min(W - 1, x + hw);
+                n += (int32_t)(__ldg(foff + (size_t)row * W + x1 + 1) - __ldg(foff + (size_t)row * W + x0));
+            }
+            cov_n[p] = n;
+        }
+        PixelFrame f = pixel_frame(x, y, W, H, Rp, sg, amin2);
+        fconst[p] = make_float4(-f.ks, -f.kt, f.m, __int_as_float(Rp));
+    }
+}
+
+// Section 6.2 in gather form: the next footprint radius of each pixel is the
+// mean of the previous radii over its 3x3 neighbourhood (clipped at the
+// border), times 4 below 4 samples, times 0.7 above 32 (no count: times 1),
+// clamped; single precision with one rounding per operation, in the same
+// order as a plain loop over the neighbourhood rows.
+__global__ void __launch_bounds__(256) k_coverage_update(int W, int H, const float *__restrict__ r_prev,
+                                                         const int32_t *__restrict__ n_prev, float r_min,
+                                                         float r_max, float *__restrict__ r_next) {
+    int P = W * H;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        const int x = p % W, y = p / W;
+        float sum = 0.f;
+        int cnt = 0;
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int qx = x + dx, qy = y + dy;
+                if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
+                sum = __fadd_rn(sum, __ldg(r_prev + (size_t)qy * W + qx));
+                ++cnt;
+            }
+        const float mean = __fdiv_rn(sum, (float)cnt);
+        const int32_t n = n_prev[p];
+        const float f = n < 0 ? 1.f : n < 4 ? 4.f : n > 32 ? 0.7f : 1.f;
+        float r = __fmul_rn(mean, f);
+        if (r < r_min) r = r_min;
+        if (r > r_max) r = r_max;
+        r_next[p] = r;
+    }
+}
+
+__global__ void k_coverage_init(int P, float r0, float *__restrict__ r, int32_t *__restrict__ n) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        r[p] = r0;
+        n[p] = -1;
     }
 }
 
@@ -280,36 +333,61 @@ __device__ __forceinline__ void advance(Cursor &k, uint32_t j, const QuadSmem &s
 }
 
 // One 2x2 pixel block (top-left pixel bx, by) by one warp.
-template <int CT, bool KAHAN>
-__device__ __forceinline__ void filter_block(int W, int H, int R, int bx, int by, const float4 *__restrict__ fconst,
+// VAR: each pixel's footprint radius is read from its gather constants
+// (adaptive footprints); otherwise every pixel uses Rfix.
+template <int CT, bool KAHAN, bool VAR>
+__device__ __forceinline__ void filter_block(int W, int H, int Rfix, int bx, int by, const float4 *__restrict__ fconst,
                                              const uint32_t *__restrict__ foff, const float4 *__restrict__ fpos,
                                              const void *__restrict__ fcol, float4 *__restrict__ out,
                                              QuadSmem &sm) {
     using CS = ColorStore<CT>;
     const int lane = threadIdx.x & 31;
-    const int span = 2 * R + 2, nv = span;
-    const bool col1 = bx + 1 < W, row1 = by + 1 < H;
-    float4 fc = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 fc = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));   // -1: no pixel
     if (lane < 4) {
         const int x = bx + (lane & 1), y = by + (lane >> 1);
         if (x < W && y < H) fc = __ldg(fconst + (size_t)y * W + x);
     }
     float nks[4], nkt[4], mk[4];
+    int Rk[4];   // footprint radius of each pixel, -1 outside the image
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         nks[k] = __shfl_sync(0xffffffffu, fc.x, k);
         nkt[k] = __shfl_sync(0xffffffffu, fc.y, k);
         mk[k] = __shfl_sync(0xffffffffu, fc.z, k);
+        if (VAR) Rk[k] = __shfl_sync(0xffffffffu, __float_as_int(fc.w), k);
+        else Rk[k] = (bx + (k & 1) < W && by + (k >> 1) < H) ? Rfix : -1;
     }
-    // union rows: lane v (< nv) takes bin row by + v - R
+    const int R = VAR ? max(max(Rk[0], Rk[1]), max(Rk[2], Rk[3])) : Rfix;   // the block's largest footprint
+    const int span = 2 * R + 2, nv = span;
+    // union rows: lane v (< nv) takes bin row by + v - R; the union of the
+    // four discs' rows is one run of columns [bx + lo, bx + hi]
     uint32_t cnt = 0, first = 0;
     if (lane < nv) {
         const int v = lane - R, row = by + v;
-        const int h0 = (v >= -R && v <= R) ? half_width(R, v) : -1;
-        const int h1 = (row1 && v - 1 >= -R && v - 1 <= R) ? half_width(R, v - 1) : -1;
-        const int hm = max(h0, h1);
-        if (hm >= 0 && row >= 0 && row < H) {
-            const int c0 = max(0, bx - hm), c1 = min(W - 1, bx + (col1 ? 1 : 0) + hm);
+        int lo = 1 << 20, hi = -(1 << 20);
+        if (VAR) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int dv = v - (k >> 1);
+                if (Rk[k] >= 0 && dv >= -Rk[k] && dv <= Rk[k]) {
+                    const int h = half_width(Rk[k], dv);
+                    lo = min(lo, (k & 1) - h);
+                    hi = max(hi, (k & 1) + h);
+                }
+            }
+        } else {
+            // two pixel rows, one radius: the union row spans the wider half-width
+            const bool col1 = bx + 1 < W, row1 = by + 1 < H;
+            const int h0 = (v >= -R && v <= R) ? half_width(R, v) : -1;
+            const int h1 = (row1 && v - 1 >= -R && v - 1 <= R) ? half_width(R, v - 1) : -1;
+            const int hm = max(h0, h1);
+            if (hm >= 0) {
+                lo = -hm;
+                hi = (col1 ? 1 : 0) + hm;
+            }
+        }
+        if (lo <= hi && row >= 0 && row < H) {
+            const int c0 = max(0, bx + lo), c1 = min(W - 1, bx + hi);
             const size_t q = (size_t)row * W;
             first = __ldg(foff + q + c0);
             cnt = __ldg(foff + q + c1 + 1) - first;
@@ -323,15 +401,15 @@ __device__ __forceinline__ void filter_block(int W, int H, int R, int bx, int by
     }
     if (lane == 0) sm.rstart[0] = 0;
     // shift table: entry (v, u) of pixel k = (kx, ky) is its shift if
-    // (u - kx)^2 + (v - ky)^2 <= R^2 and the pixel lies in the image
-    const bool valid[4] = {true, col1, row1, col1 && row1};
+    // (u - kx)^2 + (v - ky)^2 <= R_k^2 (the pixel's own disc; none outside
+    // the image)
     for (int t = lane; t < nv * span; t += 32) {
         const int v = t / span - R, u = t % span - R;
         float s4[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int du = u - (k & 1), dv = v - (k >> 1);
-            s4[k] = (valid[k] && du * du + dv * dv <= R * R) ? mk[k] : -INFINITY;
+            s4[k] = (Rk[k] >= 0 && du * du + dv * dv <= Rk[k] * Rk[k]) ? mk[k] : -INFINITY;
         }
         sm.shift[t] = make_float4(s4[0], s4[1], s4[2], s4[3]);
     }
@@ -405,7 +483,7 @@ __device__ __forceinline__ void filter_block(int W, int H, int R, int bx, int by
 
 // Tile of (2 * tbx) x (2 * 32 / tbx) pixels per CTA: 32 blocks of 2x2, four
 // per warp.
-template <int CT, bool KAHAN>
+template <int CT, bool KAHAN, bool VAR>
 __global__ void __launch_bounds__(256, 3) k_filter(int W, int H, int R, int tbx, const float4 *__restrict__ fconst,
                                                    const uint32_t *__restrict__ foff, const float4 *__restrict__ fpos,
                                                    const void *__restrict__ fcol, float4 *__restrict__ out) {
@@ -415,7 +493,7 @@ __global__ void __launch_bounds__(256, 3) k_filter(int W, int H, int R, int tbx,
     for (int blk = warp; blk < 32; blk += kWarps) {
         const int bx = blockIdx.x * 2 * tbx + (blk % tbx) * 2, by = blockIdx.y * 2 * tby + (blk / tbx) * 2;
         if (bx >= W || by >= H) continue;   // warp-uniform
-        filter_block<CT, KAHAN>(W, H, R, bx, by, fconst, foff, fpos, fcol, out, smem[warp]);
+        filter_block<CT, KAHAN, VAR>(W, H, R, bx, by, fconst, foff, fpos, fcol, out, smem[warp]);
     }
 }
 
@@ -459,7 +537,7 @@ __global__ void __launch_bounds__(256) k_batch_sigma(const BatchCtx *__restrict_
             const float2 sg = make_float2(w.ss, w.st);
             ctx.sigma[p] = sg;
             const PixelFrame f = pixel_frame(px, py, W, H, ctx.R, sg, ctx.amin2);
-            ctx.fconst[p] = make_float4(-f.ks, -f.kt, f.m, 0.f);
+            ctx.fconst[p] = make_float4(-f.ks, -f.kt, f.m, __int_as_float(ctx.R));
         }
         __syncthreads();
     }
@@ -492,7 +570,8 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchCtx *__restrict__ c
         for (int blk = warp; blk < 32; blk += kWarps) {
             const int bx = tile * tw + (blk % tbx) * 2, by = band * th + (blk / tbx) * 2;
             if (bx >= x.W || by >= x.H) continue;
-            filter_block<CT, KAHAN>(x.W, x.H, x.R, bx, by, x.fconst, x.foff, x.fpos, x.fcol, x.out, smem[warp]);
+            filter_block<CT, KAHAN, false>(x.W, x.H, x.R, bx, by, x.fconst, x.foff, x.fpos, x.fcol, x.out,
+                                           smem[warp]);
         }
         __syncthreads();
     }
@@ -650,34 +729,53 @@ const dim3 kQuadBlock(256);
 
 }  // namespace
 
-cudaError_t launch_sigma(AfrContext *c, const AfrParams *prm, bool keep, cudaStream_t s) {
-#define AFR_SIGMA(K)                                                                                           \
-    k_sigma<K><<<grid_for(c->P, 256), 256, 0, s>>>(c->W, c->H, c->R, c->S, c->ntx, c->cfg.window, c->cfg.eps_grad, \
-                                                   *prm, c->grad, c->tiles, c->amin2, c->sigma, c->fconst)
-    if (keep) AFR_SIGMA(true);
-    else AFR_SIGMA(false);
+cudaError_t launch_sigma(AfrContext *c, const AfrParams *prm, bool keep, bool adaptive, cudaStream_t s) {
+    const int g = grid_for(c->P, 256);
+    const float *radius = nullptr;
+    if (adaptive) {
+        float *next = c->cov_r[1 - c->cov_cur];
+        k_coverage_update<<<g, 256, 0, s>>>(c->W, c->H, c->cov_r[c->cov_cur], c->cov_n, 0.5f, 8.f, next);
+        c->cov_cur = 1 - c->cov_cur;
+        radius = next;
+    }
+#define AFR_SIGMA(K, A)                                                                                         \
+    k_sigma<K, A><<<g, 256, 0, s>>>(c->W, c->H, c->R, c->S, c->ntx, c->cfg.window, c->cfg.eps_grad, *prm, c->grad, \
+                                    c->tiles, c->amin2, radius, c->foff, c->cov_n, c->sigma, c->fconst)
+    if (keep && adaptive) AFR_SIGMA(true, true);
+    else if (keep) AFR_SIGMA(true, false);
+    else if (adaptive) AFR_SIGMA(false, true);
+    else AFR_SIGMA(false, false);
 #undef AFR_SIGMA
     return cudaGetLastError();
 }
 
-cudaError_t launch_filter(AfrContext *c, float t_now, float4 *out, cudaStream_t s) {
+cudaError_t launch_coverage_init(AfrContext *c, cudaStream_t s) {
+    k_coverage_init<<<grid_for(c->P, 256), 256, 0, s>>>(c->P, (float)c->R, c->cov_r[c->cov_cur], c->cov_n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_filter(AfrContext *c, float t_now, bool adaptive, float4 *out, cudaStream_t s) {
     (void)t_now;
     const int tbx = c->tile_bx, tw = 2 * tbx, th = 2 * (32 / tbx);
     dim3 grid((c->W + tw - 1) / tw, (c->H + th - 1) / th);
+#define AFR_FILTER(CT_, K_, V_)                                                                          \
+    k_filter<CT_, K_, V_><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, tbx, c->fconst, c->foff, c->fpos, c->fcol, \
+                                                      out)
     switch (c->ct) {
         case AFR_F32:
-            k_filter<AFR_F32, false><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, tbx, c->fconst, c->foff,
-                                                                     c->fpos, c->fcol, out);
+            if (adaptive) AFR_FILTER(AFR_F32, false, true);
+            else AFR_FILTER(AFR_F32, false, false);
             break;
         case AFR_F16:
-            k_filter<AFR_F16, true><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, tbx, c->fconst, c->foff,
-                                                                    c->fpos, c->fcol, out);
+            if (adaptive) AFR_FILTER(AFR_F16, true, true);
+            else AFR_FILTER(AFR_F16, true, false);
             break;
         default:
-            k_filter<AFR_BF16, true><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, tbx, c->fconst, c->foff,
-                                                                     c->fpos, c->fcol, out);
+            if (adaptive) AFR_FILTER(AFR_BF16, true, true);
+            else AFR_FILTER(AFR_BF16, true, false);
             break;
     }
+#undef AFR_FILTER
     return cudaGetLastError();
 }
 
