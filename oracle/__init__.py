@@ -17,6 +17,9 @@ Parity status of each function (what pins it, in tests/test_oracle_pins.py):
 * filter      -- pinned: constant colour, partition of unity, one- and
                  two-sample closed forms, brute force, a numpy scatter sum.
 * backward    -- pinned: central finite differences of the oracle's forward.
+* tile error  -- pinned: hand-computed shares, the partition identity
+                 sum E / s = kappa + lambda + (1 - kappa - lambda), a constant-
+                 age ramp scene for the gain control.
 * coverage    -- pinned: hand-computed updates (growth, shrinkage, clamps,
                  border means), a numpy count of records per disc, hole
                  filling, and the per-pixel-radius filter against brute force
@@ -77,6 +80,8 @@ def lib():
             L.afo_filter.argtypes = [i32, i32, i32, P, P, f32, P, P, P, i64, P]
             L.afo_filter_brute.restype = None
             L.afo_filter_brute.argtypes = [i32, i32, i32, i64, P, f32, P, P, P]
+            L.afo_tile_error.restype = None
+            L.afo_tile_error.argtypes = [i32, i32, i32, i32, P, P, f32, P, P, f64, f64, f64, f64, P, P]
             L.afo_coverage_update.restype = None
             L.afo_coverage_update.argtypes = [i32, i32, P, P, f32, f32, P, P]
             L.afo_coverage_count.restype = None
@@ -141,6 +146,19 @@ def tile_feedback(ring: Ring, grads, S: int = 32, t_now: float = 1.0, m: float =
     lib().afo_tile_feedback(ring.W, ring.H, ring.b, S, _p(ring.count), _p(ring.slot), t_now,
                             _p(gx), _p(gy), _p(gt), m, _p(out))
     return out
+
+
+def tile_error(ring: Ring, tiles, S: int = 32, t_now: float = 1.0, occluded=None, kappa: float = 0.5,
+               lam: float = 0.5, importance: float = 1.0, eps: float = 1e-4):
+    """Per-tile error E and gain control (dC/ds, dC/dt, T, S*, N*) from the
+    records of tile_feedback (sections 6.1 and 4.1)."""
+    tiles = np.ascontiguousarray(tiles, np.float64)
+    E = np.zeros(tiles.shape[0])
+    gain = np.zeros(5)
+    occ = None if occluded is None else np.ascontiguousarray(occluded, np.float64)
+    lib().afo_tile_error(ring.W, ring.H, ring.b, S, _p(ring.count), _p(ring.slot), t_now, _p(tiles),
+                         None if occ is None else _p(occ), kappa, lam, importance, eps, _p(E), _p(gain))
+    return E, gain
 
 
 def reproject(ring: Ring, t_now: float = 1.0):

@@ -441,6 +441,72 @@ void afo_filter_brute(int W, int H, int R, int64_t n, const float *rec, float t_
 }
 
 /* ------------------------------------------------------------------------ */
+/* Section 6.1: a tile's error mixes its share of the colour variation, of the
+ * undersampling and of the occlusion over all tiles, scaled by its size.
+ * Section 4.1: the gain control balances spatial change across a tile
+ * against temporal change over the samples' ages, dC/ds S = i dC/dt T. */
+void afo_tile_error(int W, int H, int b, int S, const int32_t *count, const float *slot,
+                    float t_now, const double *tiles, const double *occluded, double kappa,
+                    double lambda, double importance, double eps, double *E, double *gain)
+{
+    int ntx = (W + S - 1) / S, nty = (H + S - 1) / S, nt = ntx * nty;
+    double sv = 0.0, su = 0.0, so = 0.0, sgs = 0.0, sgt = 0.0, nonempty = 0.0, sage = 0.0, nage = 0.0;
+    for (int t = 0; t < nt; ++t) {
+        int tx = t % ntx, ty = t / ntx;
+        int x0 = tx * S, y0 = ty * S;
+        int x1 = x0 + S < W ? x0 + S : W, y1 = y0 + S < H ? y0 + S : H;
+        double A = (double)(x1 - x0) * (y1 - y0);
+        const double *r = tiles + (size_t)t * AFO_NT;
+        sv += r[AFO_TVARL];
+        su += r[AFO_TU];
+        if (occluded) so += occluded[t] / (A * b);
+        /* the tile records hold means over non-empty pixels: undo them */
+        double ne = 0.0, age = 0.0;
+        for (int y = y0; y < y1; ++y)
+            for (int x = x0; x < x1; ++x) {
+                size_t p = (size_t)y * W + x;
+                if (count[p] > 0) ne += 1.0;
+                for (int k = 0; k < count[p]; ++k) {
+                    double a = (double)t_now - (double)sample_at(slot, b, p, k)[AFO_T];
+                    age += a > 0.0 ? a : 0.0;
+                }
+            }
+        sgs += 0.5 * (r[AFO_TGX] + r[AFO_TGY]) * ne;
+        sgt += r[AFO_TGT] * ne;
+        nonempty += ne;
+        if (r[AFO_TN] > 0.0) {
+            sage += age / r[AFO_TN];
+            nage += 1.0;
+        }
+    }
+    for (int t = 0; t < nt; ++t) {
+        int tx = t % ntx, ty = t / ntx;
+        int x0 = tx * S, y0 = ty * S;
+        int x1 = x0 + S < W ? x0 + S : W, y1 = y0 + S < H ? y0 + S : H;
+        double A = (double)(x1 - x0) * (y1 - y0);
+        const double *r = tiles + (size_t)t * AFO_NT;
+        double e = 0.0;
+        if (sv > 0.0) e += kappa * r[AFO_TVARL] / sv;
+        if (su > 0.0) e += lambda * r[AFO_TU] / su;
+        if (occluded && so > 0.0) e += (1.0 - kappa - lambda) * (occluded[t] / (A * b)) / so;
+        E[t] = A * e;
+    }
+    double dcds = nonempty > 0.0 ? sgs / nonempty : 0.0;
+    double dcdt = nonempty > 0.0 ? sgt / nonempty : 0.0;
+    double T = nage > 0.0 ? sage / nage : 0.0;
+    double Sw = importance * dcdt * T / (dcds > eps ? dcds : eps);
+    double P = (double)W * H;
+    double N = Sw > 0.0 ? P / (Sw * Sw) : P;
+    if (N < 1.0) N = 1.0;
+    if (N > P) N = P;
+    gain[0] = dcds;
+    gain[1] = dcdt;
+    gain[2] = T;
+    gain[3] = Sw;
+    gain[4] = N;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Section 6.2: splat sizes follow the previous image's coverage map. A region
  * keeps the mean size used there, grows it fourfold where a pixel received
  * fewer than 4 samples and shrinks it by 0.7 where more than 32 reached it. */

@@ -75,6 +75,20 @@ void afo_filter(int W, int H, int R, const uint32_t *off, const float *rec,
 void afo_filter_brute(int W, int H, int R, int64_t n, const float *rec, float t_now,
                       const double *sig_s, const double *sig_t, double *out);
 
+/* Sections 6.1 and 4.1: tile error and gain control from the records of
+ * afo_tile_feedback (AFO_NT doubles per tile). occluded: occluded samples per
+ * tile (NULL: none). E[t] = s_t (kappa v_t / sum v + lambda u_t / sum u +
+ * (1 - kappa - lambda) o_t / sum o) with s_t the tile's pixel count and
+ * o_t = occluded_t / (s_t b); a term whose sum over tiles is 0 adds 0.
+ * gain[5] = (dC/ds, dC/dt, T, S*, N*): the image means over non-empty pixels
+ * of (G_x + G_y) / 2 and of G_t, the mean over tiles holding samples of their
+ * mean sample age max(0, t_now - t), the tile width S* = importance dC/dt T /
+ * max(dC/ds, eps) that balances the two, and the tile count W H / S*^2
+ * clamped to [1, W H]. */
+void afo_tile_error(int W, int H, int b, int S, const int32_t *count, const float *slot,
+                    float t_now, const double *tiles, const double *occluded, double kappa,
+                    double lambda, double importance, double eps, double *E, double *gain);
+
 /* Section 6.2, coverage map, in gather form: the footprint radius of each
  * pixel for the next image is the mean of the radii used for the previous
  * image over the pixel's 3x3 neighbourhood (clipped at the border), times 4

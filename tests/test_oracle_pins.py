@@ -615,3 +615,59 @@ def test_coverage_fills_a_disocclusion_hole():
     assert (second["R"][holes] == 4).all()
     assert (second["image"][:, 3] > 0).all()
     np.testing.assert_allclose(second["image"][:, :3], 0.5, rtol=1e-12)
+
+
+# ---- sections 6.1 and 4.1: tile error and gain control ------------------------
+
+def test_tile_error_hand_example():
+    """Two 2x2 tiles, b = 2: E = s (kappa v / sum v + lambda u / sum u +
+    (1 - kappa - lambda) o / sum o) with o = occluded / (s b), worked by hand."""
+    ring = oracle.Ring(4, 2, 2)                       # empty: the records below are given
+    tiles = np.zeros((2, oracle.NT))
+    tiles[:, 3] = [1.0, 3.0]                          # variance of luminance
+    tiles[:, 7] = [0.5, 0.0]                          # undersampling u
+    E, _ = oracle.tile_error(ring, tiles, S=2, occluded=[2.0, 6.0], kappa=0.5, lam=0.3)
+    np.testing.assert_allclose(E, [4 * (0.5 * 0.25 + 0.3 * 1.0 + 0.2 * 0.25),
+                                   4 * (0.5 * 0.75 + 0.0 + 0.2 * 0.75)], rtol=1e-14)
+    # without occlusion data, or with all-zero sums, a term adds nothing
+    E, _ = oracle.tile_error(ring, tiles, S=2, kappa=0.5, lam=0.3)
+    np.testing.assert_allclose(E, [4 * (0.125 + 0.3), 4 * 0.375], rtol=1e-14)
+    tiles[:, 7] = 0.0
+    E, _ = oracle.tile_error(ring, tiles, S=2, kappa=0.5, lam=0.3)
+    np.testing.assert_allclose(E, [0.5, 1.5], rtol=1e-14)
+
+
+def test_tile_error_shares_sum_to_the_weights():
+    """Each term is a share of a sum over tiles: sum_t E_t / s_t = kappa +
+    lambda + (1 - kappa - lambda) whenever every sum is positive."""
+    rng = np.random.default_rng(21)
+    W, H, b = 70, 45, 4
+    pos, col, mo = _batch(rng, W * H * 8, W, H)
+    keep = (pos[:, 0] < 48) | (pos[:, 1] < 16) | (rng.uniform(0, 1, len(pos)) < 0.05)   # a sparse corner
+    pos, col, mo = pos[keep], col[keep], mo[keep]
+    ring = oracle.Ring(W, H, b)
+    ring.insert(pos, col, mo)
+    grads = oracle.gradients(ring)
+    tiles = oracle.tile_feedback(ring, grads, S=16)
+    occ = rng.integers(0, 5, tiles.shape[0]).astype(np.float64)
+    E, _ = oracle.tile_error(ring, tiles, S=16, occluded=occ, kappa=0.3, lam=0.45)
+    ntx = -(-W // 16)
+    A = np.array([min(16, W - (t % ntx) * 16) * min(16, H - (t // ntx) * 16) for t in range(len(E))])
+    assert (tiles[:, 7] > 0).any() and tiles[:, 3].sum() > 0
+    np.testing.assert_allclose((E / A).sum(), 1.0, rtol=1e-12)
+
+
+def test_gain_control_on_a_ramp_in_space_and_time():
+    """Grey colour a x + c t at pixel centres, sampled at t = 0.25 and 0.75:
+    G_x = a, G_y = 0, G_t = c everywhere, every sample age is 0.75 or 0.25, so
+    dC/ds = a / 2, dC/dt = c, T = 0.5 and S* = i c T / (a / 2)."""
+    a, c, i = 0.02, 0.3, 1.5
+    W, H = 40, 24
+    ring = _grid_ring(W, H, 4, lambda x, y, t: (a * x + c * t,) * 3)
+    grads = oracle.gradients(ring)
+    tiles = oracle.tile_feedback(ring, grads, S=8)
+    _, gain = oracle.tile_error(ring, tiles, S=8, importance=i)
+    dcds, dcdt, T, Sw, N = gain
+    np.testing.assert_allclose([dcds, dcdt, T], [a / 2, c, 0.5], rtol=1e-5)
+    np.testing.assert_allclose(Sw, i * c * 0.5 / (a / 2), rtol=1e-5)
+    np.testing.assert_allclose(N, max(1.0, W * H / Sw ** 2), rtol=1e-5)
