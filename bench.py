@@ -271,7 +271,7 @@ def run_ours(args, rank, world):
     # adaptive footprints (section 6.2): successive reconstructions of the
     # same frame view, each sizing footprints from the previous one's coverage
     from paper_2510_15876_gb300 import _lib as L
-    adapt = {}
+    adapt, tile_err = {}, {}
     if not args.quick:
         _, pos, col, mo, out, tiles = keep
         step(rec, pos, col, mo, out, tiles)
@@ -298,6 +298,18 @@ def run_ours(args, rank, world):
         rec.reconstruct(T_NOW, out=out, flags=flags)
         torch.cuda.synchronize()
         adapt["holes_adaptive"] = int((out[..., 3] == 0).sum())
+        # tile error and gain control (sections 6.1, 4.1) on the same buffer
+        E, gain = rec.tile_error(0.5, 0.5, 1.0)
+        s4, e4 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s4.record()
+        for _ in range(args.steps):
+            rec.tile_error(0.5, 0.5, 1.0)
+        e4.record()
+        torch.cuda.synchronize()
+        tile_err = {"ms_per_call": round(s4.elapsed_time(e4) / args.steps, 4), "tiles": int(E.numel()),
+                    "gain": {k: round(v, 6) for k, v in gain.items()},
+                    "what": "afr_tile_error (kappa = lambda = 0.5, no occlusion data), including the device-to-host "
+                            "read of the gain record"}
 
     # end to end through the public API, batch in pinned host memory: every
     # step copies its inputs host -> device and its image device -> host inside
@@ -381,6 +393,7 @@ def run_ours(args, rank, world):
                             for ct in results},
         "fwd_bwd": fb,
         "adaptive_footprint": adapt,
+        "tile_error": tile_err,
         "batched": batched,
         "e2e": {"value": round(world * 1000.0 / e2e_ms, 3), "unit": "reconstructions/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4),

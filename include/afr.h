@@ -173,6 +173,29 @@ AFR_API AfrStatus afr_reconstruct(AfrContext *ctx, float t_now, const AfrParams 
  * Requires afr_estimate_gradients since the last insertion. */
 AFR_API AfrStatus afr_tile_feedback(AfrContext *ctx, AfrTileStats *out_dev, afr_stream_t stream);
 
+/* Sections 6.1 and 4.1: the sampler's tile error and gain control, from the
+ * tile statistics of the last afr_estimate_gradients (afr_tile_feedback need
+ * not be called first). error_dev (device, n_tiles floats, required) gets
+ * E_t = s_t (kappa v_t / sum v + lambda u_t / sum u
+ *            + (1 - kappa - lambda) o_t / sum o),
+ * s_t the tile's pixel count, v_t the age-weighted luminance variance, u_t
+ * the undersampling measure, o_t = occluded_t / (s_t b) from occluded_dev
+ * (device, n_tiles counts of occluded samples found by the caller's own
+ * occlusion test; NULL: no occlusion data); a term whose sum over tiles is 0
+ * adds 0. gain_dev (device, may be NULL) gets the gain control: the image
+ * means over non-empty pixels of (G_x + G_y) / 2 and of G_t, the mean over
+ * tiles holding samples of their mean sample age, the tile width S* =
+ * importance dC/dt T / max(dC/ds, eps_grad) that balances spatial and
+ * temporal change (dC/ds S = i dC/dt T), and the tile count W H / S*^2
+ * clamped to [1, W H]. Requires 0 <= kappa, lambda and kappa + lambda <= 1,
+ * importance >= 0 (else AFR_ERR_INVALID_ARG). */
+typedef struct {
+    float dC_ds, dC_dt, mean_age, tile_width, tile_count;
+} AfrGain;
+AFR_API AfrStatus afr_tile_error(AfrContext *ctx, float kappa, float lambda, float importance,
+                                 const uint32_t *occluded_dev, float *error_dev, AfrGain *gain_dev,
+                                 afr_stream_t stream);
+
 /* Adjoint of afr_reconstruct (no counterpart in the paper, which does not
  * differentiate its filter). grad_rgb_dev: width*height float4, the loss
  * gradient with respect to each output (r, g, b); its 4th lane is ignored

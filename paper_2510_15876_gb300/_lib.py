@@ -28,7 +28,7 @@ EXPORTED = [
     "afr_reproject", "afr_reconstruct", "afr_reconstruct_ex", "afr_tile_feedback", "afr_reconstruct_backward",
     "afr_get_status", "afr_last_error", "afr_query", "afr_num_tiles", "afr_export_ring", "afr_export_frame",
     "afr_export_map", "afr_import_map", "afr_set_frame_colors", "afr_reproject_batch_static", "afr_set_tuning",
-    "afr_profile_filter", "afr_profile_read",
+    "afr_profile_filter", "afr_profile_read", "afr_tile_error",
     "afr_batch_create", "afr_batch_destroy", "afr_batch_reconstruct",
 ]
 
@@ -88,6 +88,7 @@ def _declare(L):
                                            c_p, c_p, c_p, c_p, c_p, c_p]),
         "afr_set_tuning": (S, [c_p, c_i32, c_i32]),
         "afr_profile_filter": (S, [c_p, c_i32]),
+        "afr_tile_error": (S, [c_p, c_f32, c_f32, c_f32, c_p, c_p, c_p, c_p]),
         "afr_profile_read": (S, [c_p, c_p, c_i32, ctypes.POINTER(c_i32)]),
         "afr_batch_create": (S, [ctypes.POINTER(c_p), c_i32, ctypes.POINTER(c_p)]),
         "afr_batch_destroy": (None, [c_p]),

@@ -122,6 +122,22 @@ class Reconstructor:
         self._check(self.lib.afr_tile_feedback(self.h, _ptr(out), _stream(stream)))
         return out
 
+    def tile_error(self, kappa: float = 0.5, lam: float = 0.5, importance: float = 1.0,
+                   occluded: torch.Tensor | None = None, stream=None):
+        """Per-tile error E (sections 6.1) as a [n_tiles] float32 tensor and the
+        gain control (section 4.1) as a dict."""
+        E = torch.empty(self.n_tiles, dtype=torch.float32, device=self.device)
+        g = torch.empty(5, dtype=torch.float32, device=self.device)
+        occ = None
+        if occluded is not None:
+            occ = occluded.to(self.device, torch.int32).contiguous()
+            if occ.numel() != self.n_tiles:
+                raise ValueError(f"occluded needs {self.n_tiles} counts")
+        self._check(self.lib.afr_tile_error(self.h, kappa, lam, importance, _ptr(occ), _ptr(E), _ptr(g),
+                                            _stream(stream)))
+        keys = ("dC_ds", "dC_dt", "mean_age", "tile_width", "tile_count")
+        return E, dict(zip(keys, g.cpu().tolist()))
+
     def backward(self, grad_rgbw: torch.Tensor, want_colors: bool = True, want_params: bool = True,
                  n_frame: int | None = None, stream=None):
         grad_rgbw = grad_rgbw.contiguous()

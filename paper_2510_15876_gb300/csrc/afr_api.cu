@@ -35,7 +35,7 @@ cudaError_t dalloc(T **p, size_t n) {
 void free_all(AfrContext *c) {
     void *ptrs[] = {c->r_xy, c->r_mo, c->r_t, c->r_depth, c->r_seq, c->r_col, c->r_state, c->bin_of,
                     c->pack,
-                    c->pcnt, c->poff, c->lbar, c->grad, c->pstat, c->sigma, c->fconst, c->cov_r[0], c->cov_r[1], c->cov_n, c->amin2, c->tiles, c->fcnt,
+                    c->pcnt, c->poff, c->lbar, c->grad, c->pstat, c->sigma, c->tile_age, c->fconst, c->cov_r[0], c->cov_r[1], c->cov_n, c->amin2, c->tiles, c->fcnt,
                     c->foff, c->fpos, c->fcol, c->fseq, c->scan_tmp, c->bgrad, c->bparam, c->dcount, c->derr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -156,6 +156,7 @@ AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
     AFR_ALLOC(c->pstat, P);
     AFR_ALLOC(c->sigma, P);
     AFR_ALLOC(c->fconst, P);
+    AFR_ALLOC(c->tile_age, (size_t)c->ntiles);
     AFR_ALLOC(c->cov_r[0], P);
     AFR_ALLOC(c->cov_r[1], P);
     AFR_ALLOC(c->cov_n, P);
@@ -338,6 +339,20 @@ AfrStatus afr_tile_feedback(AfrContext *c, AfrTileStats *out_dev, afr_stream_t s
     if (!c->grads_valid) return fail(c, AFR_ERR_BAD_STATE, "afr_tile_feedback: call afr_estimate_gradients first");
     cudaError_t e = afr::launch_feedback(c, out_dev, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(c, e, "afr_tile_feedback");
+    return AFR_OK;
+}
+
+AfrStatus afr_tile_error(AfrContext *c, float kappa, float lambda, float importance, const uint32_t *occluded_dev,
+                         float *error_dev, AfrGain *gain_dev, afr_stream_t stream) {
+    if (!c) return AFR_ERR_INVALID_ARG;
+    if (!error_dev) return fail(c, AFR_ERR_INVALID_ARG, "afr_tile_error: null output");
+    if (!(kappa >= 0.f && lambda >= 0.f && kappa + lambda <= 1.f) || !(importance >= 0.f) || !std::isfinite(importance))
+        return fail(c, AFR_ERR_INVALID_ARG, "afr_tile_error: need 0 <= kappa, lambda, kappa + lambda <= 1, importance >= 0");
+    if (gain_dev && !aligned(gain_dev, 4)) return fail(c, AFR_ERR_INVALID_ARG, "afr_tile_error: misaligned gain");
+    if (!c->grads_valid) return fail(c, AFR_ERR_BAD_STATE, "afr_tile_error: call afr_estimate_gradients first");
+    cudaError_t e = afr::launch_tile_error(c, kappa, lambda, importance, occluded_dev, error_dev, gain_dev,
+                                           reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(c, e, "afr_tile_error");
     return AFR_OK;
 }
 

@@ -85,6 +85,7 @@ struct AfrContext {
     float4 *grad = nullptr;       // [P] (Gx, Gy, Gt, Lbar)
     float4 *pstat = nullptr;      // [P] (sum w, mean L, M2, Gt)
     float2 *sigma = nullptr;      // [P] (sigma_s, sigma_t)
+    double *tile_age = nullptr;   // [ntiles] sum of sample ages per tile (afr_tile_error)
     float4 *fconst = nullptr;     // [P] gather constants (-ks, -kt, exponent shift m, disc radius as int bits)
     float *cov_r[2] = {nullptr, nullptr};   // [P] footprint radii of adaptive reconstructions (ping-pong)
     int32_t *cov_n = nullptr;     // [P] samples in each pixel's footprint in the last adaptive reconstruction
@@ -222,6 +223,8 @@ cudaError_t launch_sigma(AfrContext *c, const AfrParams *prm, bool keep, bool ad
 cudaError_t launch_coverage_init(AfrContext *c, cudaStream_t s);
 cudaError_t launch_filter(AfrContext *c, float t_now, bool adaptive, float4 *out, cudaStream_t s);
 cudaError_t launch_feedback(AfrContext *c, AfrTileStats *out, cudaStream_t s);
+cudaError_t launch_tile_error(AfrContext *c, float kappa, float lambda, float importance, const uint32_t *occluded,
+                              float *E, AfrGain *gain, cudaStream_t s);
 cudaError_t launch_backward(AfrContext *c, const float4 *grad_rgb, float *grad_col, float *grad_prm,
                             cudaStream_t s);
 cudaError_t launch_set_frame_colors(AfrContext *c, const float *rgb, cudaStream_t s);
