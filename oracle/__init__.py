@@ -17,6 +17,8 @@ Parity status of each function (what pins it, in tests/test_oracle_pins.py):
 * filter      -- pinned: constant colour, partition of unity, one- and
                  two-sample closed forms, brute force, a numpy scatter sum.
 * backward    -- pinned: central finite differences of the oracle's forward.
+* fifo        -- pinned: a collections.deque(maxlen=N) model; its frame view
+                 against a float32 numpy reprojection of the deque.
 * tile error  -- pinned: hand-computed shares, the partition identity
                  sum E / s = kappa + lambda + (1 - kappa - lambda), a constant-
                  age ramp scene for the gain control.
@@ -80,6 +82,8 @@ def lib():
             L.afo_filter.argtypes = [i32, i32, i32, P, P, f32, P, P, P, i64, P]
             L.afo_filter_brute.restype = None
             L.afo_filter_brute.argtypes = [i32, i32, i32, i64, P, f32, P, P, P]
+            L.afo_fifo_insert.restype = i64
+            L.afo_fifo_insert.argtypes = [i32, i32, i64, P, P, P, u32, i64, P, P, P]
             L.afo_tile_error.restype = None
             L.afo_tile_error.argtypes = [i32, i32, i32, i32, P, P, f32, P, P, f64, f64, f64, f64, P, P]
             L.afo_coverage_update.restype = None
@@ -129,6 +133,54 @@ class Ring:
     @property
     def resident(self) -> int:
         return int(self.count.sum())
+
+
+class Fifo:
+    """The reconstructor's buffer of section 5.2: the N most recent accepted
+    samples of the whole image, in one queue. Sequence numbers count every
+    sample offered (accepted or not), as for the per-pixel queues."""
+
+    def __init__(self, W: int, H: int, N: int):
+        self.W, self.H, self.N = W, H, N
+        self.q = np.zeros((N, NF), np.float32)
+        self.seq = np.zeros(N, np.uint32)
+        self.accepted = ctypes.c_int64(0)
+        self.total = 0
+
+    def insert(self, pos, color, motion) -> int:
+        pos = np.ascontiguousarray(pos, np.float32)
+        color = np.ascontiguousarray(color, np.float32)
+        motion = np.ascontiguousarray(motion, np.float32)
+        n = pos.shape[0]
+        rej = lib().afo_fifo_insert(self.W, self.H, self.N, ctypes.addressof(self.accepted), _p(self.q),
+                                    _p(self.seq), self.total & 0xFFFFFFFF, n, _p(pos), _p(color), _p(motion))
+        self.total += n
+        return rej
+
+    @property
+    def resident(self) -> int:
+        return int(min(self.accepted.value, self.N))
+
+
+def reproject_fifo(fifo: Fifo, t_now: float = 1.0):
+    """reproject() over the FIFO's samples: the queue is handed to the same
+    routine as one list (a single 'pixel' holding every sample); the frame
+    view orders records by bin and sequence number, so storage order does
+    not matter."""
+    W, H, P, n = fifo.W, fifo.H, fifo.W * fifo.H, fifo.resident
+    count = np.zeros(P, np.int32)
+    count[0] = n
+    cap = max(1, n)
+    off = np.zeros(P + 1, np.uint32)
+    rec = np.zeros((cap, NR), np.float32)
+    rseq = np.zeros(cap, np.uint32)
+    dropped = ctypes.c_int64(0)
+    slot = np.ascontiguousarray(fifo.q[:max(n, 1)])
+    seq = np.ascontiguousarray(fifo.seq[:max(n, 1)])
+    m = lib().afo_reproject(W, H, max(n, 1), _p(count), _p(slot), _p(seq), t_now, _p(off), _p(rec), _p(rseq),
+                            cap, ctypes.addressof(dropped))
+    assert m >= 0
+    return off, rec[:m].copy(), rseq[:m].copy(), dropped.value
 
 
 def gradients(ring: Ring, t_now: float = 1.0):

@@ -77,6 +77,41 @@ int64_t afo_ingest(int W, int H, int b, int32_t *count, float *slot, uint32_t *s
 }
 
 /* ------------------------------------------------------------------------ */
+/* Section 5.2: the reconstructor stores the N most recent samples of the
+ * whole image in one queue ordered by time of arrival; a new sample replaces
+ * the oldest once the queue is full. */
+int64_t afo_fifo_insert(int W, int H, int64_t N, int64_t *total, float *q, uint32_t *qseq,
+                        uint32_t seq0, int64_t n, const float *pos, const float *col,
+                        const float *mo)
+{
+    int64_t rejected = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const float *ps = pos + 4 * i, *cs = col + 4 * i, *ms = mo + 2 * i;
+        float x = ps[0], y = ps[1], t = ps[2];
+        int ok = isfinite(x) && isfinite(y) && isfinite(t) && isfinite(cs[0]) &&
+                 isfinite(cs[1]) && isfinite(cs[2]) && isfinite(ms[0]) && isfinite(ms[1]);
+        if (!ok || x < 0.0f || y < 0.0f || x >= (float)W || y >= (float)H) {
+            ++rejected;
+            continue;
+        }
+        int64_t k = *total % N;
+        float *s = q + (size_t)k * AFO_NF;
+        s[AFO_X] = x;
+        s[AFO_Y] = y;
+        s[AFO_T] = t;
+        s[AFO_DEPTH] = ps[3];
+        s[AFO_R] = cs[0];
+        s[AFO_G] = cs[1];
+        s[AFO_B] = cs[2];
+        s[AFO_MX] = ms[0];
+        s[AFO_MY] = ms[1];
+        qseq[k] = seq0 + (uint32_t)i;
+        *total += 1;
+    }
+    return rejected;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Sections 4 and 4.1. The pixel's luminance is the age-weighted mean of its
  * queue. The spatial gradient in x is the mean of the one-sided absolute
  * luminance differences to the left and right neighbours (those that exist

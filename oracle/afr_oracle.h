@@ -32,6 +32,15 @@ enum { AFO_TN = 0, AFO_TEMPTY, AFO_TMEANL, AFO_TVARL, AFO_TGX, AFO_TGY, AFO_TGT,
 /* filter parameters theta */
 enum { AFO_ALPHA_S = 0, AFO_BETA_S, AFO_CLAMP_S, AFO_ALPHA_T, AFO_BETA_T, AFO_CLAMP_T, AFO_NP };
 
+/* Section 5.2: the reconstructor's own deep buffer, one temporally ordered
+ * queue of the N most recent samples over the whole image. Accepted samples
+ * (as afo_ingest accepts them) of the batch enter in index order at slot
+ * (*total mod N); *total counts the accepted samples so far. Returns the
+ * number rejected. q holds N*AFO_NF floats, qseq N sequence numbers. */
+int64_t afo_fifo_insert(int W, int H, int64_t N, int64_t *total, float *q, uint32_t *qseq,
+                        uint32_t seq0, int64_t n, const float *pos, const float *col,
+                        const float *mo);
+
 /* Section 4: push a batch into the per-pixel deep-buffer queues. Returns the
  * number of rejected samples. seq of sample i is seq0 + i. */
 int64_t afo_ingest(int W, int H, int b, int32_t *count, float *slot, uint32_t *seq,

@@ -671,3 +671,59 @@ def test_gain_control_on_a_ramp_in_space_and_time():
     np.testing.assert_allclose([dcds, dcdt, T], [a / 2, c, 0.5], rtol=1e-5)
     np.testing.assert_allclose(Sw, i * c * 0.5 / (a / 2), rtol=1e-5)
     np.testing.assert_allclose(N, max(1.0, W * H / Sw ** 2), rtol=1e-5)
+
+
+# ---- section 5.2: the reconstructor's global FIFO buffer ---------------------------
+
+def test_fifo_keeps_the_n_most_recent_accepted_samples():
+    rng = np.random.default_rng(31)
+    W, H, N = 9, 7, 37
+    fifo = oracle.Fifo(W, H, N)
+    model = collections.deque(maxlen=N)
+    seq = 0
+    for n in (20, 31, 5, 60):
+        pos, col, mo = _batch(rng, n, W, H, bad_frac=0.2)
+        rej = fifo.insert(pos, col, mo)
+        bad = 0
+        for i in range(n):
+            x, y, t = pos[i, 0], pos[i, 1], pos[i, 2]
+            vals = [x, y, t, col[i, 0], col[i, 1], col[i, 2], mo[i, 0], mo[i, 1]]
+            if not all(np.isfinite(vals)) or not (0 <= x < W and 0 <= y < H):
+                bad += 1
+                continue
+            model.append((seq + i, [x, y, t, pos[i, 3], col[i, 0], col[i, 1], col[i, 2], mo[i, 0], mo[i, 1]]))
+        seq += n
+        assert rej == bad
+        k = fifo.resident
+        assert k == len(model)
+        got = sorted(zip(fifo.seq[:k].tolist(), fifo.q[:k].tolist()))
+        want = [(s, list(np.float32(v))) for s, v in model]
+        assert [s for s, _ in got] == [s for s, _ in want]
+        np.testing.assert_array_equal(np.array([v for _, v in got], np.float32),
+                                      np.array([v for _, v in want], np.float32))
+
+
+def test_fifo_frame_view_matches_float32_model():
+    """The FIFO's frame view: every sample moved in single precision with one
+    rounding per operation, off-image ones dropped, the rest ordered by bin
+    and sequence number."""
+    rng = np.random.default_rng(32)
+    W, H, N = 17, 12, 300
+    fifo = oracle.Fifo(W, H, N)
+    for n in (250, 180):
+        fifo.insert(*_batch(rng, n, W, H))
+    off, rec, rseq, dropped = oracle.reproject_fifo(fifo, 1.0)
+    k = fifo.resident
+    q, sq = fifo.q[:k], fifo.seq[:k]
+    a = np.float32(1.0) - q[:, 2]
+    xp = q[:, 0] + q[:, 7] * a
+    yp = q[:, 1] + q[:, 8] * a
+    ok = (xp >= 0) & (xp < W) & (yp >= 0) & (yp < H)
+    assert dropped == int((~ok).sum())
+    bins = np.floor(yp[ok]).astype(np.int64) * W + np.floor(xp[ok]).astype(np.int64)
+    order = np.lexsort((sq[ok], bins))
+    np.testing.assert_array_equal(rseq, sq[ok][order])
+    np.testing.assert_array_equal(rec[:, 0], xp[ok][order])
+    np.testing.assert_array_equal(rec[:, 1], yp[ok][order])
+    np.testing.assert_array_equal(rec[:, 3:6], q[ok][order][:, 4:7])
+    np.testing.assert_array_equal(np.diff(off.astype(np.int64)), np.bincount(bins, minlength=W * H))
