@@ -66,6 +66,10 @@ typedef struct {
     float window;            /* length of the time window in its own units (default 1) */
     float eps_grad;          /* floor of the gradients in the extent rule (default 1e-4) */
     float undersample_m;     /* m of the undersampling measure (default 2) */
+    uint32_t fifo_capacity;  /* section 5.2: 0 (default) reprojects the per-pixel queues; N > 0
+                                also keeps the N most recent accepted samples of the whole
+                                image in one queue, and afr_reproject builds the frame view
+                                from that queue instead (N <= 2^28) */
 } AfrConfig;
 
 /* Mapping from filter extents to Gaussian widths (theta). Section 5.1 sizes
@@ -120,7 +124,8 @@ AFR_API AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out);
 /* Frees everything the context owns. Safe on NULL. Synchronises the device. */
 AFR_API void afr_destroy(AfrContext *ctx);
 
-/* Empties the deep buffer and restarts sequence numbering. */
+/* Empties the deep buffer (and the reconstructor's queue of a context with
+ * fifo_capacity > 0) and restarts sequence numbering. */
 AFR_API AfrStatus afr_reset(AfrContext *ctx, afr_stream_t stream);
 
 /* Grows the context's ingest scratch to hold batches of up to n samples so
@@ -147,7 +152,9 @@ AFR_API AfrStatus afr_insert_samples(AfrContext *ctx, const AfrSampleBatch *batc
  * partial statistics that afr_tile_feedback and afr_reconstruct read. */
 AFR_API AfrStatus afr_estimate_gradients(AfrContext *ctx, float t_now, afr_stream_t stream);
 
-/* Section 6.2: moves every buffered sample to t_now along its motion,
+/* Section 6.2: moves every buffered sample (with fifo_capacity N > 0: every
+ * sample of the reconstructor's queue of the N most recent accepted samples,
+ * section 5.2) to t_now along its motion,
  * x' = x + m_x (t_now - t) in single precision with one rounding per
  * operation, and bins it at the pixel holding x' into the frame view.
  * Samples leaving the image are dropped and counted. Within a bin, records

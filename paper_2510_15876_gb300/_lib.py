@@ -35,7 +35,8 @@ EXPORTED = [
 
 class AfrConfig(ctypes.Structure):
     _fields_ = [("width", c_i32), ("height", c_i32), ("depth", c_i32), ("tile", c_i32), ("radius", c_i32),
-                ("color_type", c_i32), ("window", c_f32), ("eps_grad", c_f32), ("undersample_m", c_f32)]
+                ("color_type", c_i32), ("window", c_f32), ("eps_grad", c_f32), ("undersample_m", c_f32),
+                ("fifo_capacity", c_u32)]
 
 
 class AfrParams(ctypes.Structure):

@@ -42,7 +42,7 @@ class Reconstructor:
 
     def __init__(self, width: int, height: int, depth: int, *, tile: int = 32, radius: int = 4,
                  color_type: str = "f32", window: float = 1.0, eps_grad: float = 1e-4,
-                 undersample_m: float = 2.0, device=None):
+                 undersample_m: float = 2.0, fifo_capacity: int = 0, device=None):
         self.lib = L.load()
         self.device = torch.device(device if device is not None else "cuda")
         if self.device.type != "cuda":
@@ -51,7 +51,7 @@ class Reconstructor:
         self.W, self.H, self.b, self.S, self.R = width, height, depth, tile, radius
         self.ct = _COLOR_TYPES[color_type]
         self.color_dtype = _COLOR_DTYPES[self.ct]
-        cfg = L.AfrConfig(width, height, depth, tile, radius, self.ct, window, eps_grad, undersample_m)
+        cfg = L.AfrConfig(width, height, depth, tile, radius, self.ct, window, eps_grad, undersample_m, fifo_capacity)
         h = ctypes.c_void_p()
         st = self.lib.afr_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != L.AFR_OK:

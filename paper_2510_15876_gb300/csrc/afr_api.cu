@@ -36,7 +36,7 @@ void free_all(AfrContext *c) {
     void *ptrs[] = {c->r_xy, c->r_mo, c->r_t, c->r_depth, c->r_seq, c->r_col, c->r_state, c->bin_of,
                     c->pack,
                     c->pcnt, c->poff, c->lbar, c->grad, c->pstat, c->sigma, c->tile_age, c->fconst, c->cov_r[0], c->cov_r[1], c->cov_n, c->amin2, c->tiles, c->fcnt,
-                    c->foff, c->fpos, c->fcol, c->fseq, c->scan_tmp, c->bgrad, c->bparam, c->dcount, c->derr};
+                    c->foff, c->fpos, c->fcol, c->fseq, c->q_xy, c->q_mo, c->q_t, c->q_seq, c->q_col, c->q_total, c->scan_tmp, c->bgrad, c->bparam, c->dcount, c->derr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -115,6 +115,7 @@ AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
         !(g.eps_grad > 0.f) || !(g.undersample_m >= 0.f))
         return AFR_ERR_INVALID_ARG;
     if ((size_t)g.width * g.height * g.depth > (1ull << 28)) return AFR_ERR_INVALID_ARG;
+    if (g.fifo_capacity > (1u << 28)) return AFR_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();
@@ -135,7 +136,8 @@ AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
     c->ntiles = c->ntx * c->nty;
     c->nslots = (size_t)c->P * c->b;
     c->csize = c->ct == AFR_F32 ? 16 : 8;
-    c->frame_cap = c->nslots;
+    c->fifo_n = g.fifo_capacity;
+    c->frame_cap = std::max(c->nslots, c->fifo_n);
     c->scan_tmp_n = afr::scan_tmp_elems(c->P);
     c->n_bblocks = afr::backward_blocks(c->W, c->H);
     cudaError_t e = cudaSuccess;
@@ -164,9 +166,19 @@ AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
     AFR_ALLOC(c->tiles, (size_t)c->ntiles);
     AFR_ALLOC(c->fcnt, P);
     AFR_ALLOC(c->foff, P + 1);
-    AFR_ALLOC(c->fpos, 2 * N);
-    if (e == cudaSuccess) e = cudaMalloc(&c->fcol, 2 * N * c->csize);
-    AFR_ALLOC(c->fseq, 2 * N);
+    if (c->fifo_n) {
+        const size_t Q = c->fifo_n;
+        AFR_ALLOC(c->q_xy, Q);
+        AFR_ALLOC(c->q_mo, Q);
+        AFR_ALLOC(c->q_t, Q);
+        AFR_ALLOC(c->q_seq, Q);
+        if (e == cudaSuccess) e = cudaMalloc(&c->q_col, Q * c->csize);
+        AFR_ALLOC(c->q_total, 1);
+        if (e == cudaSuccess) e = cudaMemset(c->q_total, 0, sizeof(uint32_t));
+    }
+    AFR_ALLOC(c->fpos, 2 * c->frame_cap);
+    if (e == cudaSuccess) e = cudaMalloc(&c->fcol, 2 * c->frame_cap * c->csize);
+    AFR_ALLOC(c->fseq, 2 * c->frame_cap);
     AFR_ALLOC(c->scan_tmp, c->scan_tmp_n);
     AFR_ALLOC(c->bgrad, 2 * P);
     AFR_ALLOC(c->bparam, (size_t)c->n_bblocks * 6);
@@ -207,6 +219,7 @@ AfrStatus afr_reset(AfrContext *c, afr_stream_t stream) {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(c->r_state, 0, (size_t)c->P * sizeof(uint32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->dcount, 0, afr::CNT_N * sizeof(unsigned long long), s);
+    if (e == cudaSuccess && c->q_total) e = cudaMemsetAsync(c->q_total, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return cuda_fail(c, e, "afr_reset");
     c->inserted = 0;
     c->grads_valid = c->frame_valid = c->recon_valid = false;
@@ -215,9 +228,10 @@ AfrStatus afr_reset(AfrContext *c, afr_stream_t stream) {
 }
 
 static void free_batch(AfrContext *c) {
-    void *ptrs[] = {c->bin_of, c->pack};
+    void *ptrs[] = {c->bin_of, c->pack, c->fifo_flag, c->fifo_rank, c->fifo_scan};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    c->fifo_flag = c->fifo_rank = c->fifo_scan = nullptr;
     c->bin_of = nullptr;
     c->pack = nullptr;
     c->batch_cap = 0;
@@ -231,6 +245,11 @@ AfrStatus afr_reserve(AfrContext *c, uint32_t n) {
     free_batch(c);
     e = dalloc(&c->bin_of, n);
     if (e == cudaSuccess) e = cudaMalloc(&c->pack, (size_t)n * afr::packed_bytes(c->ct));
+    if (c->fifo_n) {
+        if (e == cudaSuccess) e = dalloc(&c->fifo_flag, n);
+        if (e == cudaSuccess) e = dalloc(&c->fifo_rank, n);
+        if (e == cudaSuccess) e = dalloc(&c->fifo_scan, afr::scan_tmp_elems(n));
+    }
     if (e != cudaSuccess) {
         free_batch(c);
         cudaGetLastError();
@@ -253,6 +272,7 @@ AfrStatus afr_insert_samples(AfrContext *c, const AfrSampleBatch *batch, uint32_
     if (st != AFR_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = afr::launch_ingest(c, batch, n, (uint32_t)c->inserted, s);
+    if (e == cudaSuccess && c->fifo_n) e = afr::launch_fifo_append(c, batch, n, (uint32_t)c->inserted, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "afr_insert_samples");
     c->inserted += n;
     c->grads_valid = c->frame_valid = c->recon_valid = false;

@@ -74,6 +74,14 @@ struct AfrContext {
     uint32_t *r_state = nullptr;  // count | head << 16
 
     // ingest scratch
+    // reconstructor queue of section 5.2 (fifo_capacity > 0): slot k of N
+    size_t fifo_n = 0;
+    float2 *q_xy = nullptr, *q_mo = nullptr;
+    float *q_t = nullptr;
+    uint32_t *q_seq = nullptr;
+    void *q_col = nullptr;
+    uint32_t *q_total = nullptr;  // [1] accepted samples so far (the next slot is q_total mod N)
+    uint32_t *fifo_flag = nullptr, *fifo_rank = nullptr, *fifo_scan = nullptr;   // per batch
     uint2 *bin_of = nullptr;      // [batch_cap] (pixel, ticket within the pixel) of each sample (kInvalid: rejected)
     void *pack = nullptr;         // [batch_cap] 64-byte sample records in pixel order
     size_t batch_cap = 0;
@@ -217,6 +225,7 @@ size_t scan_tmp_elems(size_t n);
 
 cudaError_t launch_ingest(AfrContext *c, const AfrSampleBatch *batch, uint32_t n, uint32_t seq0,
                           cudaStream_t s);
+cudaError_t launch_fifo_append(AfrContext *c, const AfrSampleBatch *batch, uint32_t n, uint32_t seq0, cudaStream_t s);
 cudaError_t launch_gradients(AfrContext *c, float t_now, cudaStream_t s);
 cudaError_t launch_reproject(AfrContext *c, float t_now, cudaStream_t s);
 cudaError_t launch_sigma(AfrContext *c, const AfrParams *prm, bool keep, bool adaptive, cudaStream_t s);

@@ -252,7 +252,69 @@ cudaError_t run(AfrContext *c, const float4 *pos, const void *col, const float2 
     return cudaGetLastError();
 }
 
+// ---- reconstructor queue (section 5.2) ----------------------------------------
+// The batch's accepted samples (k_hist marked the rejected ones) enter the
+// N-slot queue in index order: a scan gives each its rank r among the
+// batch's accepted samples, and it lands at slot (total + r) mod N; of a batch
+// with more than N accepted samples only the last N are written.
+__global__ void __launch_bounds__(256) k_fifo_flag(const uint2 *__restrict__ bin_of, uint32_t n,
+                                                   uint32_t *__restrict__ flag) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        flag[i] = bin_of[i].x != kInvalid ? 1u : 0u;
+}
+
+template <int CT>
+__global__ void __launch_bounds__(256) k_fifo_append(const float4 *__restrict__ pos, const void *__restrict__ col,
+                                                     const float2 *__restrict__ mo, uint32_t n,
+                                                     const uint32_t *__restrict__ flag,
+                                                     const uint32_t *__restrict__ rank, uint32_t seq0, uint32_t N,
+                                                     const uint32_t *__restrict__ total, float2 *__restrict__ q_xy,
+                                                     float2 *__restrict__ q_mo, float *__restrict__ q_t,
+                                                     uint32_t *__restrict__ q_seq, void *__restrict__ q_col) {
+    using CS = ColorStore<CT>;
+    const uint32_t accepted = rank[n - 1] + flag[n - 1], t0 = *total;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (!flag[i] || (uint64_t)rank[i] + N < accepted) continue;
+        const uint32_t k = (uint32_t)(((uint64_t)t0 + rank[i]) % N);
+        const float4 p = __ldg(pos + i);
+        q_xy[k] = make_float2(p.x, p.y);
+        q_t[k] = p.z;
+        q_mo[k] = __ldg(mo + i);
+        q_seq[k] = seq0 + i;
+        reinterpret_cast<typename CS::T *>(q_col)[k] = CS::raw(col, i);
+    }
+}
+
+__global__ void k_fifo_advance(const uint32_t *__restrict__ flag, const uint32_t *__restrict__ rank, uint32_t n,
+                               uint32_t *__restrict__ total) {
+    *total += rank[n - 1] + flag[n - 1];
+}
+
+template <int CT>
+cudaError_t run_fifo(AfrContext *c, const float4 *pos, const void *col, const float2 *mo, uint32_t n, uint32_t seq0,
+                     cudaStream_t s) {
+    const int g = grid_for(n, 256);
+    k_fifo_flag<<<g, 256, 0, s>>>(c->bin_of, n, c->fifo_flag);
+    cudaError_t e = scan_exclusive(c->fifo_flag, c->fifo_rank, n, c->fifo_scan, s);
+    if (e != cudaSuccess) return e;
+    k_fifo_append<CT><<<g, 256, 0, s>>>(pos, col, mo, n, c->fifo_flag, c->fifo_rank, seq0, (uint32_t)c->fifo_n,
+                                        c->q_total, c->q_xy, c->q_mo, c->q_t, c->q_seq, c->q_col);
+    k_fifo_advance<<<1, 1, 0, s>>>(c->fifo_flag, c->fifo_rank, n, c->q_total);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_fifo_append(AfrContext *c, const AfrSampleBatch *batch, uint32_t n, uint32_t seq0,
+                               cudaStream_t s) {
+    const float4 *pos = reinterpret_cast<const float4 *>(batch->pos_dev);
+    const float2 *mo = reinterpret_cast<const float2 *>(batch->motion_dev);
+    switch (c->ct) {
+        case AFR_F32: return run_fifo<AFR_F32>(c, pos, batch->color_dev, mo, n, seq0, s);
+        case AFR_F16: return run_fifo<AFR_F16>(c, pos, batch->color_dev, mo, n, seq0, s);
+        default: return run_fifo<AFR_BF16>(c, pos, batch->color_dev, mo, n, seq0, s);
+    }
+}
 
 size_t packed_bytes(int) { return sizeof(Rec64); }
 

@@ -52,16 +52,24 @@ __device__ __forceinline__ bool slot_live(uint32_t st, int s, int b) {
     return age < n;
 }
 
+// FIFO: the slots are the reconstructor queue's, live below min(*state, nslots)
+// (state then points at its count of accepted samples).
+template <bool FIFO>
 __global__ void __launch_bounds__(256) k_count(uint32_t nslots, int b, int bshift, int W, int H, float t_now,
                                                const uint32_t *__restrict__ state, const float2 *__restrict__ r_xy,
                                                const float2 *__restrict__ r_mo, const float *__restrict__ r_t,
                                                uint32_t *__restrict__ fcnt, uint32_t *__restrict__ amin2,
                                                unsigned long long *__restrict__ dcount) {
+    const uint32_t nlive = FIFO ? min(__ldg(state), nslots) : 0u;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nslots; i += gridDim.x * blockDim.x) {
-        uint32_t p;
-        int s;
-        split_slot(i, b, bshift, p, s);
-        if (!slot_live(__ldg(state + p), s, b)) continue;
+        if (FIFO) {
+            if (i >= nlive) continue;
+        } else {
+            uint32_t p;
+            int s;
+            split_slot(i, b, bshift, p, s);
+            if (!slot_live(__ldg(state + p), s, b)) continue;
+        }
         Moved mv = move_sample(__ldg(r_xy + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H);
         agg_count(dcount + CNT_DROPPED, !mv.ok);
         if (!mv.ok) continue;
@@ -73,7 +81,7 @@ __global__ void __launch_bounds__(256) k_count(uint32_t nslots, int b, int bshif
     }
 }
 
-template <int CT>
+template <int CT, bool FIFO>
 __global__ void __launch_bounds__(256) k_scatter(uint32_t nslots, int b, int bshift, int W, int H, float t_now,
                                                  const uint32_t *__restrict__ state, const float2 *__restrict__ r_xy,
                                                  const float2 *__restrict__ r_mo, const float *__restrict__ r_t,
@@ -82,11 +90,16 @@ __global__ void __launch_bounds__(256) k_scatter(uint32_t nslots, int b, int bsh
                                                  float4 *__restrict__ fpos, void *__restrict__ fcol,
                                                  uint32_t *__restrict__ fseq) {
     using CS = ColorStore<CT>;
+    const uint32_t nlive = FIFO ? min(__ldg(state), nslots) : 0u;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nslots; i += gridDim.x * blockDim.x) {
-        uint32_t p;
-        int s;
-        split_slot(i, b, bshift, p, s);
-        if (!slot_live(__ldg(state + p), s, b)) continue;
+        if (FIFO) {
+            if (i >= nlive) continue;
+        } else {
+            uint32_t p;
+            int s;
+            split_slot(i, b, bshift, p, s);
+            if (!slot_live(__ldg(state + p), s, b)) continue;
+        }
         Moved mv = move_sample(__ldg(r_xy + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H);
         if (!mv.ok) continue;
         uint32_t e = __ldg(foff + mv.bin) + agg_inc(fcur, mv.bin);
@@ -139,11 +152,23 @@ cudaError_t launch_reproject(AfrContext *c, float t_now, cudaStream_t s) {
     if ((e = cudaMemsetAsync(c->fcnt, 0, sizeof(uint32_t) * c->P, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->dcount + CNT_DROPPED, 0, sizeof(unsigned long long) * 2, s)) != cudaSuccess) return e;
     k_fill_u32<<<grid_for(c->P, 256), 256, 0, s>>>(c->amin2, c->P, 0x7f800000u);
-    int g = grid_for(c->nslots, 256);
-    const uint32_t ns = (uint32_t)c->nslots;
+    // source: the per-pixel queues, or the reconstructor queue (section 5.2)
+    const bool fifo = c->fifo_n > 0;
+    const size_t nsrc = fifo ? c->fifo_n : c->nslots;
+    const uint32_t *state = fifo ? c->q_total : c->r_state;
+    const float2 *xy = fifo ? c->q_xy : c->r_xy, *mo = fifo ? c->q_mo : c->r_mo;
+    const float *tt = fifo ? c->q_t : c->r_t;
+    const uint32_t *sq = fifo ? c->q_seq : c->r_seq;
+    const void *col = fifo ? c->q_col : c->r_col;
+    const int g = grid_for(nsrc, 256);
+    const uint32_t ns = (uint32_t)nsrc;
     const int bshift = (c->b & (c->b - 1)) == 0 ? __builtin_ctz((unsigned)c->b) : -1;
-    k_count<<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, c->r_state, c->r_xy, c->r_mo, c->r_t, c->fcnt,
-                              c->amin2, c->dcount);
+    if (fifo)
+        k_count<true><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, state, xy, mo, tt, c->fcnt, c->amin2,
+                                        c->dcount);
+    else
+        k_count<false><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, state, xy, mo, tt, c->fcnt, c->amin2,
+                                         c->dcount);
     if ((e = scan_exclusive(c->fcnt, c->foff, c->P, c->scan_tmp, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->fcnt, 0, sizeof(uint32_t) * c->P, s)) != cudaSuccess) return e;
     // records land unordered in the second half of the buffers, then k_order
@@ -151,27 +176,23 @@ cudaError_t launch_reproject(AfrContext *c, float t_now, cudaStream_t s) {
     float4 *tmp_pos = c->fpos + c->frame_cap;
     void *tmp_col = static_cast<char *>(c->fcol) + c->frame_cap * c->csize;
     uint32_t *tmp_seq = c->fseq + c->frame_cap;
-    int go = grid_for(c->nslots, 256);
+#define AFR_REPROJ(CT_)                                                                                        \
+    do {                                                                                                       \
+        if (fifo)                                                                                              \
+            k_scatter<CT_, true><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, state, xy, mo, tt, sq, col, \
+                                                   c->foff, c->fcnt, tmp_pos, tmp_col, tmp_seq);              \
+        else                                                                                                   \
+            k_scatter<CT_, false><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, state, xy, mo, tt, sq,     \
+                                                    col, c->foff, c->fcnt, tmp_pos, tmp_col, tmp_seq);        \
+        k_order<CT_><<<g, 256, 0, s>>>(c->W, c->foff, (uint32_t)c->P, tmp_pos, tmp_col, tmp_seq, c->fpos, c->fcol, \
+                                       c->fseq, c->dcount);                                                    \
+    } while (0)
     switch (c->ct) {
-        case AFR_F32:
-            k_scatter<AFR_F32><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, c->r_state, c->r_xy, c->r_mo, c->r_t,
-                                                 c->r_seq, c->r_col, c->foff, c->fcnt, tmp_pos, tmp_col, tmp_seq);
-            k_order<AFR_F32><<<go, 256, 0, s>>>(c->W, c->foff, (uint32_t)c->P, tmp_pos, tmp_col, tmp_seq, c->fpos, c->fcol,
-                                                 c->fseq, c->dcount);
-            break;
-        case AFR_F16:
-            k_scatter<AFR_F16><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, c->r_state, c->r_xy, c->r_mo, c->r_t,
-                                                 c->r_seq, c->r_col, c->foff, c->fcnt, tmp_pos, tmp_col, tmp_seq);
-            k_order<AFR_F16><<<go, 256, 0, s>>>(c->W, c->foff, (uint32_t)c->P, tmp_pos, tmp_col, tmp_seq, c->fpos, c->fcol,
-                                                 c->fseq, c->dcount);
-            break;
-        default:
-            k_scatter<AFR_BF16><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, c->r_state, c->r_xy, c->r_mo, c->r_t,
-                                                  c->r_seq, c->r_col, c->foff, c->fcnt, tmp_pos, tmp_col, tmp_seq);
-            k_order<AFR_BF16><<<go, 256, 0, s>>>(c->W, c->foff, (uint32_t)c->P, tmp_pos, tmp_col, tmp_seq, c->fpos, c->fcol,
-                                                 c->fseq, c->dcount);
-            break;
+        case AFR_F32: AFR_REPROJ(AFR_F32); break;
+        case AFR_F16: AFR_REPROJ(AFR_F16); break;
+        default: AFR_REPROJ(AFR_BF16); break;
     }
+#undef AFR_REPROJ
     return cudaGetLastError();
 }
 
