@@ -247,7 +247,7 @@ AfrStatus afr_reserve(AfrContext *c, uint32_t n) {
     if (e == cudaSuccess) e = cudaMalloc(&c->pack, (size_t)n * afr::packed_bytes(c->ct));
     if (c->fifo_n) {
         if (e == cudaSuccess) e = dalloc(&c->fifo_flag, n);
-        if (e == cudaSuccess) e = dalloc(&c->fifo_rank, n);
+        if (e == cudaSuccess) e = dalloc(&c->fifo_rank, (size_t)n + 1);   // the scan also writes the total
         if (e == cudaSuccess) e = dalloc(&c->fifo_scan, afr::scan_tmp_elems(n));
     }
     if (e != cudaSuccess) {

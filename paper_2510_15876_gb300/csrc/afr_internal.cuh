@@ -81,7 +81,9 @@ struct AfrContext {
     uint32_t *q_seq = nullptr;
     void *q_col = nullptr;
     uint32_t *q_total = nullptr;  // [1] accepted samples so far (the next slot is q_total mod N)
-    uint32_t *fifo_flag = nullptr, *fifo_rank = nullptr, *fifo_scan = nullptr;   // per batch
+    uint32_t *fifo_flag = nullptr;  // [batch_cap] 1 for an accepted sample
+    uint32_t *fifo_rank = nullptr;  // [batch_cap + 1] exclusive scan of fifo_flag, then the total
+    uint32_t *fifo_scan = nullptr;  // scan block sums for batch_cap entries
     uint2 *bin_of = nullptr;      // [batch_cap] (pixel, ticket within the pixel) of each sample (kInvalid: rejected)
     void *pack = nullptr;         // [batch_cap] 64-byte sample records in pixel order
     size_t batch_cap = 0;
