@@ -12,7 +12,10 @@ The same run also times the FP16- and BF16-stored forms of that step, the
 forward+backward of the 512x512x8 differentiation workload, the batched form
 (48 streams, one persistent launch in a CUDA graph, against 48 sequential
 single-stream launches), the step end to end through the Python API with the
-batch in pinned host memory, and the CPU oracle on a band of the workload.
+batch in pinned host memory, adaptive footprints (section 6.2), the tile
+error and gain control (6.1, 4.1), the global FIFO buffer against the
+per-pixel queues (5.2, on the 1024x1024x8 workload), and the CPU oracle on a
+band of the workload.
 
 Prints one JSON line. --impl reference times the CPU oracle instead (a band
 of the same workload per step, scaled to whole images).
