@@ -17,6 +17,9 @@ Parity status of each function (what pins it, in tests/test_oracle_pins.py):
 * filter      -- pinned: constant colour, partition of unity, one- and
                  two-sample closed forms, brute force, a numpy scatter sum.
 * backward    -- pinned: central finite differences of the oracle's forward.
+* camera      -- pinned: a float32 numpy projection model, the identity camera
+                 (screen points map to themselves), a camera pan equal to a
+                 screen shift, points behind the camera dropped.
 * fifo        -- pinned: a collections.deque(maxlen=N) model; its frame view
                  against a float32 numpy reprojection of the deque.
 * tile error  -- pinned: hand-computed shares, the partition identity
@@ -82,6 +85,8 @@ def lib():
             L.afo_filter.argtypes = [i32, i32, i32, P, P, f32, P, P, P, i64, P]
             L.afo_filter_brute.restype = None
             L.afo_filter_brute.argtypes = [i32, i32, i32, i64, P, f32, P, P, P]
+            L.afo_reproject_camera.restype = i64
+            L.afo_reproject_camera.argtypes = [i32, i32, i32, P, P, P, P, P, f32, P, P, P, i64, P]
             L.afo_fifo_insert.restype = i64
             L.afo_fifo_insert.argtypes = [i32, i32, i64, P, P, P, u32, i64, P, P, P]
             L.afo_tile_error.restype = None
@@ -133,6 +138,25 @@ class Ring:
     @property
     def resident(self) -> int:
         return int(self.count.sum())
+
+
+def reproject_camera(ring: Ring, world_by_seq, view_proj, t_now: float = 1.0):
+    """reproject() with the stored 3D hit points rendered by the row-major 4x4
+    view_proj (section 6.2); world_by_seq[seq] = (X, Y, Z, -) of every sample
+    inserted so far, indexed by sequence number."""
+    P = ring.W * ring.H
+    cap = max(1, ring.resident)
+    off = np.zeros(P + 1, np.uint32)
+    rec = np.zeros((cap, NR), np.float32)
+    rseq = np.zeros(cap, np.uint32)
+    dropped = ctypes.c_int64(0)
+    world = np.ascontiguousarray(world_by_seq, np.float32).reshape(-1, 4)
+    vp = np.ascontiguousarray(view_proj, np.float32).reshape(16)
+    n = lib().afo_reproject_camera(ring.W, ring.H, ring.b, _p(ring.count), _p(ring.slot), _p(ring.seq),
+                                   _p(world), _p(vp), t_now, _p(off), _p(rec), _p(rseq), cap,
+                                   ctypes.addressof(dropped))
+    assert n >= 0
+    return off, rec[:n].copy(), rseq[:n].copy(), dropped.value
 
 
 class Fifo:

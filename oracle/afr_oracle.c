@@ -325,6 +325,80 @@ int64_t afo_reproject(int W, int H, int b, const int32_t *count, const float *sl
     return (int64_t)n;
 }
 
+/* Section 6.2: the reconstructor reprojects by rendering the stored hit points
+ * with the current camera; a sample's own motion (if any) is added on screen. */
+static int project(const float *vp, const float *w, int W, int H, float *sx, float *sy)
+{
+    float cx = vp[0] * w[0];
+    cx = cx + vp[1] * w[1];
+    cx = cx + vp[2] * w[2];
+    cx = cx + vp[3];
+    float cy = vp[4] * w[0];
+    cy = cy + vp[5] * w[1];
+    cy = cy + vp[6] * w[2];
+    cy = cy + vp[7];
+    float cw = vp[12] * w[0];
+    cw = cw + vp[13] * w[1];
+    cw = cw + vp[14] * w[2];
+    cw = cw + vp[15];
+    if (!(cw > 0.0f)) return 0;
+    float nx = cx / cw, ny = cy / cw;
+    *sx = (nx * 0.5f + 0.5f) * (float)W;
+    *sy = (ny * 0.5f + 0.5f) * (float)H;
+    return 1;
+}
+
+int64_t afo_reproject_camera(int W, int H, int b, const int32_t *count, const float *slot,
+                             const uint32_t *seq, const float *world_by_seq, const float *vp,
+                             float t_now, uint32_t *off, float *rec, uint32_t *rseq, int64_t cap,
+                             int64_t *dropped)
+{
+    size_t P = (size_t)W * H, total = 0;
+    for (size_t p = 0; p < P; ++p) total += (size_t)count[p];
+    ReprojEntry *e = (ReprojEntry *)malloc(sizeof(ReprojEntry) * (total ? total : 1));
+    size_t n = 0;
+    int64_t drop = 0;
+    for (size_t p = 0; p < P; ++p) {
+        for (int k = 0; k < count[p]; ++k) {
+            const float *s = sample_at(slot, b, p, k);
+            uint32_t sq = seq[p * b + k];
+            float sx, sy;
+            int front = project(vp, world_by_seq + (size_t)sq * 4, W, H, &sx, &sy);
+            float a = t_now - s[AFO_T];
+            float xp = sx + s[AFO_MX] * a;
+            float yp = sy + s[AFO_MY] * a;
+            if (!front || !(xp >= 0.0f && xp < (float)W && yp >= 0.0f && yp < (float)H)) {
+                ++drop;
+                continue;
+            }
+            e[n].bin = (uint32_t)((int)floorf(yp) * W + (int)floorf(xp));
+            e[n].seq = sq;
+            e[n].v[AFO_RX] = xp;
+            e[n].v[AFO_RY] = yp;
+            e[n].v[AFO_RT] = s[AFO_T];
+            e[n].v[AFO_RR] = s[AFO_R];
+            e[n].v[AFO_RG] = s[AFO_G];
+            e[n].v[AFO_RB] = s[AFO_B];
+            ++n;
+        }
+    }
+    if (dropped) *dropped = drop;
+    if ((int64_t)n > cap) {
+        free(e);
+        return -1;
+    }
+    qsort(e, n, sizeof(ReprojEntry), entry_cmp);
+    for (size_t q = 0; q <= P; ++q) off[q] = 0;
+    for (size_t i = 0; i < n; ++i) off[e[i].bin + 1] += 1;
+    for (size_t q = 0; q < P; ++q) off[q + 1] += off[q];
+    for (size_t i = 0; i < n; ++i) {
+        memcpy(rec + i * AFO_NR, e[i].v, sizeof(float) * AFO_NR);
+        rseq[i] = e[i].seq;
+    }
+    free(e);
+    return (int64_t)n;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Section 5.1. The local sampling rate R_l (samples per pixel per window) is
  * read from the sampler's tiling, here the fixed tile holding the pixel, and

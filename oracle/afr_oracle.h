@@ -32,6 +32,18 @@ enum { AFO_TN = 0, AFO_TEMPTY, AFO_TMEANL, AFO_TVARL, AFO_TGX, AFO_TGY, AFO_TGT,
 /* filter parameters theta */
 enum { AFO_ALPHA_S = 0, AFO_BETA_S, AFO_CLAMP_S, AFO_ALPHA_T, AFO_BETA_T, AFO_CLAMP_T, AFO_NP };
 
+/* Section 6.2 with camera matrices: every resident sample's 3D hit point
+ * (world_by_seq[4*seq .. 4*seq+2], looked up by its sequence number) is
+ * projected with the row-major 4x4 matrix vp: c = vp (X, Y, Z, 1), each row
+ * summed left to right; x' = (c_x / c_w * 1/2 + 1/2) W + m_x a and
+ * y' = (c_y / c_w * 1/2 + 1/2) H + m_y a with a = t_now - t, single
+ * precision, one rounding per operation. Samples with c_w <= 0 or leaving
+ * the image are dropped. Frame view as afo_reproject. */
+int64_t afo_reproject_camera(int W, int H, int b, const int32_t *count, const float *slot,
+                             const uint32_t *seq, const float *world_by_seq, const float *vp,
+                             float t_now, uint32_t *off, float *rec, uint32_t *rseq, int64_t cap,
+                             int64_t *dropped);
+
 /* Section 5.2: the reconstructor's own deep buffer, one temporally ordered
  * queue of the N most recent samples over the whole image. Accepted samples
  * (as afo_ingest accepts them) of the batch enter in index order at slot

@@ -727,3 +727,75 @@ def test_fifo_frame_view_matches_float32_model():
     np.testing.assert_array_equal(rec[:, 1], yp[ok][order])
     np.testing.assert_array_equal(rec[:, 3:6], q[ok][order][:, 4:7])
     np.testing.assert_array_equal(np.diff(off.astype(np.int64)), np.bincount(bins, minlength=W * H))
+
+
+# ---- section 6.2 with camera matrices ---------------------------------------------
+
+def _camera_ring(rng, W, H, b, n, grid=64.0):
+    """Samples whose stored hit points lie on a 1/grid lattice, so that the
+    screen mappings below are exact in single precision."""
+    ring = oracle.Ring(W, H, b)
+    X = np.floor(rng.uniform(0, W, n) * grid) / grid
+    Y = np.floor(rng.uniform(0, H, n) * grid) / grid
+    t = np.sort(rng.uniform(0, 1, n)).astype(np.float32)
+    pos = np.stack([X, Y, t, rng.uniform(0, 1, n)], 1).astype(np.float32)
+    col = np.zeros((n, 4), np.float32)
+    col[:, :3] = rng.uniform(0, 1, (n, 3))
+    ring.insert(pos, col, np.zeros((n, 2), np.float32))
+    world = np.stack([X, Y, rng.uniform(1, 5, n), np.zeros(n)], 1).astype(np.float32)
+    return ring, world
+
+
+def _screen_camera(W, H, dx=0.0, dy=0.0):
+    """World (X, Y) in pixels to NDC, the camera moved by (dx, dy) pixels."""
+    return np.array([[2 / W, 0, 0, -1 - 2 * dx / W], [0, 2 / H, 0, -1 - 2 * dy / H], [0, 0, 1, 0], [0, 0, 0, 1]],
+                    np.float32)
+
+
+def test_camera_identity_and_pan_are_exact():
+    rng = np.random.default_rng(41)
+    W, H, b = 64, 32, 4
+    ring, world = _camera_ring(rng, W, H, b, 700)
+    off, rec, rseq, dropped = oracle.reproject_camera(ring, world, _screen_camera(W, H))
+    assert dropped == 0
+    np.testing.assert_array_equal(rec[:, 0], world[rseq, 0])
+    np.testing.assert_array_equal(rec[:, 1], world[rseq, 1])
+    off2, rec2, rseq2, dropped2 = oracle.reproject_camera(ring, world, _screen_camera(W, H, dx=4.0, dy=-2.0))
+    keep = (world[rseq, 0] - 4 >= 0) & (world[rseq, 1] + 2 < H)
+    assert dropped2 == int((~keep).sum())
+    want = np.stack([world[:, 0] - 4, world[:, 1] + 2], 1)
+    np.testing.assert_array_equal(rec2[:, :2], want[rseq2])
+
+
+def test_camera_projection_matches_float32_model():
+    rng = np.random.default_rng(42)
+    W, H, b = 48, 40, 4
+    n = 900
+    ring = oracle.Ring(W, H, b)
+    pos, col, mo = _batch(rng, n, W, H)
+    ring.insert(pos, col, mo)
+    world = np.stack([rng.uniform(-2, 2, n), rng.uniform(-2, 2, n), rng.uniform(2, 6, n), np.zeros(n)],
+                     1).astype(np.float32)
+    f = np.float32
+    vp = np.array([[1.2, 0.1, 0.05, 0.02], [-0.05, 1.3, 0.1, -0.1], [0, 0, 1, 0], [0.01, 0.02, 0.4, 0.3]], f)
+    world[:7, 2] = -5.0                                    # behind the camera
+    off, rec, rseq, dropped = oracle.reproject_camera(ring, world, vp, 1.0)
+    count, slot, seq = ring.count, ring.slot, ring.seq
+    rows = []
+    for p in range(W * H):
+        for k in range(count[p]):
+            s, q = slot[p, k], seq[p, k]
+            w = world[q]
+            c = [f(f(f(vp[r, 0] * w[0]) + f(vp[r, 1] * w[1])) + f(vp[r, 2] * w[2])) + vp[r, 3] for r in (0, 1, 3)]
+            if not c[2] > 0:
+                continue
+            a = f(f(1.0) - s[2])
+            xp = f(f(f(f(c[0] / c[2]) * f(0.5)) + f(0.5)) * f(W)) + f(s[7] * a)
+            yp = f(f(f(f(c[1] / c[2]) * f(0.5)) + f(0.5)) * f(H)) + f(s[8] * a)
+            if 0 <= xp < W and 0 <= yp < H:
+                rows.append((int(np.floor(yp)) * W + int(np.floor(xp)), int(q), xp, yp))
+    rows.sort(key=lambda r: (r[0], r[1]))
+    assert dropped == ring.resident - len(rows)
+    np.testing.assert_array_equal(rseq, [r[1] for r in rows])
+    np.testing.assert_array_equal(rec[:, 0], np.array([r[2] for r in rows], np.float32))
+    np.testing.assert_array_equal(rec[:, 1], np.array([r[3] for r in rows], np.float32))
