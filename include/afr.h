@@ -70,6 +70,9 @@ typedef struct {
                                 also keeps the N most recent accepted samples of the whole
                                 image in one queue, and afr_reproject builds the frame view
                                 from that queue instead (N <= 2^28) */
+    uint32_t world_points;   /* section 6.2: nonzero if every sample carries the 3D hit point of its
+                                primary ray (AfrSampleBatch.world_dev), which the context stores
+                                for afr_reproject_camera */
 } AfrConfig;
 
 /* Mapping from filter extents to Gaussian widths (theta). Section 5.1 sizes
@@ -90,6 +93,8 @@ typedef struct {
     const void *pos_dev;
     const void *color_dev;
     const void *motion_dev;
+    const void *world_dev;   /* float4 (X, Y, Z, unused) hit point per sample, 16-byte aligned;
+                                required by contexts created with world_points, else ignored */
 } AfrSampleBatch;
 
 /* Per-tile statistics (sections 4, 4.2 and 6.1), tiles row-major over a
@@ -161,6 +166,20 @@ AFR_API AfrStatus afr_estimate_gradients(AfrContext *ctx, float t_now, afr_strea
  * are ordered by sequence number; a bin holding more than 4096 records keeps
  * arrival order instead (counted in AfrInfo.unsorted_bins). */
 AFR_API AfrStatus afr_reproject(AfrContext *ctx, float t_now, afr_stream_t stream);
+
+/* Section 6.2 with camera matrices: the frame view for t_now built by
+ * rendering every buffered sample's stored 3D hit point (X, Y, Z) with the
+ * current camera, view_proj_host (16 floats, row-major, host memory): with
+ * c = view_proj (X, Y, Z, 1) (each row summed left to right),
+ * x' = (c_x / c_w * 1/2 + 1/2) width + m_x (t_now - t) and
+ * y' = (c_y / c_w * 1/2 + 1/2) height + m_y (t_now - t), where m is the
+ * sample's own screen motion (zero for static geometry), in single precision
+ * with one rounding per operation. Samples with c_w <= 0 or leaving the image
+ * are dropped and counted; the rest are binned as afr_reproject bins them
+ * (from the reconstructor queue when fifo_capacity > 0). Requires a context
+ * created with world_points (else AFR_ERR_BAD_STATE). */
+AFR_API AfrStatus afr_reproject_camera(AfrContext *ctx, float t_now, const float *view_proj_host,
+                                       afr_stream_t stream);
 
 /* Sections 5.1 and 5.2: for every pixel, the extents e_s = cbrt(V_S G_t/G_s),
  * e_t = cbrt(V_S G_s^2/G_t^2) (V_S = tile pixels * window / tile samples,

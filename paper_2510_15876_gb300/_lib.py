@@ -28,7 +28,7 @@ EXPORTED = [
     "afr_reproject", "afr_reconstruct", "afr_reconstruct_ex", "afr_tile_feedback", "afr_reconstruct_backward",
     "afr_get_status", "afr_last_error", "afr_query", "afr_num_tiles", "afr_export_ring", "afr_export_frame",
     "afr_export_map", "afr_import_map", "afr_set_frame_colors", "afr_reproject_batch_static", "afr_set_tuning",
-    "afr_profile_filter", "afr_profile_read", "afr_tile_error",
+    "afr_profile_filter", "afr_profile_read", "afr_tile_error", "afr_reproject_camera",
     "afr_batch_create", "afr_batch_destroy", "afr_batch_reconstruct",
 ]
 
@@ -36,7 +36,7 @@ EXPORTED = [
 class AfrConfig(ctypes.Structure):
     _fields_ = [("width", c_i32), ("height", c_i32), ("depth", c_i32), ("tile", c_i32), ("radius", c_i32),
                 ("color_type", c_i32), ("window", c_f32), ("eps_grad", c_f32), ("undersample_m", c_f32),
-                ("fifo_capacity", c_u32)]
+                ("fifo_capacity", c_u32), ("world_points", c_u32)]
 
 
 class AfrParams(ctypes.Structure):
@@ -45,7 +45,7 @@ class AfrParams(ctypes.Structure):
 
 
 class AfrSampleBatch(ctypes.Structure):
-    _fields_ = [("pos_dev", c_p), ("color_dev", c_p), ("motion_dev", c_p)]
+    _fields_ = [("pos_dev", c_p), ("color_dev", c_p), ("motion_dev", c_p), ("world_dev", c_p)]
 
 
 class AfrTileStats(ctypes.Structure):
@@ -90,6 +90,7 @@ def _declare(L):
         "afr_set_tuning": (S, [c_p, c_i32, c_i32]),
         "afr_profile_filter": (S, [c_p, c_i32]),
         "afr_tile_error": (S, [c_p, c_f32, c_f32, c_f32, c_p, c_p, c_p, c_p]),
+        "afr_reproject_camera": (S, [c_p, c_f32, c_p, c_p]),
         "afr_profile_read": (S, [c_p, c_p, c_i32, ctypes.POINTER(c_i32)]),
         "afr_batch_create": (S, [ctypes.POINTER(c_p), c_i32, ctypes.POINTER(c_p)]),
         "afr_batch_destroy": (None, [c_p]),

@@ -42,7 +42,7 @@ class Reconstructor:
 
     def __init__(self, width: int, height: int, depth: int, *, tile: int = 32, radius: int = 4,
                  color_type: str = "f32", window: float = 1.0, eps_grad: float = 1e-4,
-                 undersample_m: float = 2.0, fifo_capacity: int = 0, device=None):
+                 undersample_m: float = 2.0, fifo_capacity: int = 0, world_points: bool = False, device=None):
         self.lib = L.load()
         self.device = torch.device(device if device is not None else "cuda")
         if self.device.type != "cuda":
@@ -51,7 +51,8 @@ class Reconstructor:
         self.W, self.H, self.b, self.S, self.R = width, height, depth, tile, radius
         self.ct = _COLOR_TYPES[color_type]
         self.color_dtype = _COLOR_DTYPES[self.ct]
-        cfg = L.AfrConfig(width, height, depth, tile, radius, self.ct, window, eps_grad, undersample_m, fifo_capacity)
+        cfg = L.AfrConfig(width, height, depth, tile, radius, self.ct, window, eps_grad, undersample_m, fifo_capacity,
+                          1 if world_points else 0)
         h = ctypes.c_void_p()
         st = self.lib.afr_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != L.AFR_OK:
@@ -91,12 +92,18 @@ class Reconstructor:
     def reserve(self, n: int):
         self._check(self.lib.afr_reserve(self.h, n))
 
-    def insert(self, pos: torch.Tensor, color: torch.Tensor, motion: torch.Tensor, stream=None):
+    def insert(self, pos: torch.Tensor, color: torch.Tensor, motion: torch.Tensor, world: torch.Tensor | None = None,
+               stream=None):
+        """world: [n, 4] float32 hit points (X, Y, Z, -) for world_points contexts."""
         n = pos.shape[0]
-        for t, dt, cols in ((pos, torch.float32, 4), (color, self.color_dtype, 4), (motion, torch.float32, 2)):
+        arrays = [(pos, torch.float32, 4), (color, self.color_dtype, 4), (motion, torch.float32, 2)]
+        if world is not None:
+            arrays.append((world, torch.float32, 4))
+        for t, dt, cols in arrays:
             if t.device != self.device or t.dtype != dt or not t.is_contiguous() or tuple(t.shape) != (n, cols):
                 raise ValueError(f"batch tensor must be contiguous {dt} [{n}, {cols}] on {self.device}")
-        batch = L.AfrSampleBatch(pos.data_ptr(), color.data_ptr(), motion.data_ptr())
+        batch = L.AfrSampleBatch(pos.data_ptr(), color.data_ptr(), motion.data_ptr(),
+                                 None if world is None else world.data_ptr())
         self._check(self.lib.afr_insert_samples(self.h, ctypes.byref(batch), n, _stream(stream)))
 
     def estimate_gradients(self, t_now: float = 1.0, stream=None):
@@ -104,6 +111,12 @@ class Reconstructor:
 
     def reproject(self, t_now: float = 1.0, stream=None):
         self._check(self.lib.afr_reproject(self.h, t_now, _stream(stream)))
+
+    def reproject_camera(self, t_now: float, view_proj, stream=None):
+        """Frame view from the stored hit points rendered by the row-major 4x4
+        view_proj (section 6.2)."""
+        m = (ctypes.c_float * 16)(*[float(v) for v in np.asarray(view_proj, np.float32).reshape(16)])
+        self._check(self.lib.afr_reproject_camera(self.h, t_now, m, _stream(stream)))
 
     def reconstruct(self, t_now: float = 1.0, params=None, out: torch.Tensor | None = None, flags: int = 0,
                     stream=None) -> torch.Tensor:

@@ -36,7 +36,7 @@ void free_all(AfrContext *c) {
     void *ptrs[] = {c->r_xy, c->r_mo, c->r_t, c->r_depth, c->r_seq, c->r_col, c->r_state, c->bin_of,
                     c->pack,
                     c->pcnt, c->poff, c->lbar, c->grad, c->pstat, c->sigma, c->tile_age, c->fconst, c->cov_r[0], c->cov_r[1], c->cov_n, c->amin2, c->tiles, c->fcnt,
-                    c->foff, c->fpos, c->fcol, c->fseq, c->q_xy, c->q_mo, c->q_t, c->q_seq, c->q_col, c->q_total, c->scan_tmp, c->bgrad, c->bparam, c->dcount, c->derr};
+                    c->foff, c->fpos, c->fcol, c->fseq, c->q_xy, c->q_mo, c->q_t, c->q_seq, c->q_col, c->q_total, c->q_world, c->r_world, c->scan_tmp, c->bgrad, c->bparam, c->dcount, c->derr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -166,8 +166,10 @@ AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
     AFR_ALLOC(c->tiles, (size_t)c->ntiles);
     AFR_ALLOC(c->fcnt, P);
     AFR_ALLOC(c->foff, P + 1);
+    if (g.world_points) AFR_ALLOC(c->r_world, N);
     if (c->fifo_n) {
         const size_t Q = c->fifo_n;
+        if (g.world_points) AFR_ALLOC(c->q_world, Q);
         AFR_ALLOC(c->q_xy, Q);
         AFR_ALLOC(c->q_mo, Q);
         AFR_ALLOC(c->q_t, Q);
@@ -266,6 +268,8 @@ AfrStatus afr_insert_samples(AfrContext *c, const AfrSampleBatch *batch, uint32_
         return fail(c, AFR_ERR_INVALID_ARG, "afr_insert_samples: null batch pointer");
     if (!aligned(batch->pos_dev, 16) || !aligned(batch->color_dev, c->csize) || !aligned(batch->motion_dev, 8))
         return fail(c, AFR_ERR_INVALID_ARG, "afr_insert_samples: misaligned batch array");
+    if (c->r_world && (!batch->world_dev || !aligned(batch->world_dev, 16)))
+        return fail(c, AFR_ERR_INVALID_ARG, "afr_insert_samples: this context needs 16-byte aligned world points");
     if (c->inserted + n > 0xFFFFFFFFull)
         return fail(c, AFR_ERR_INVALID_ARG, "afr_insert_samples: sequence numbers exhausted; call afr_reset");
     AfrStatus st = afr_reserve(c, n);
@@ -290,10 +294,31 @@ AfrStatus afr_estimate_gradients(AfrContext *c, float t_now, afr_stream_t stream
     return AFR_OK;
 }
 
+AfrStatus afr_reproject_camera(AfrContext *c, float t_now, const float *view_proj, afr_stream_t stream) {
+    if (!c) return AFR_ERR_INVALID_ARG;
+    if (!std::isfinite(t_now) || !view_proj)
+        return fail(c, AFR_ERR_INVALID_ARG, "afr_reproject_camera: t_now not finite or null matrix");
+    for (int k = 0; k < 16; ++k)
+        if (!std::isfinite(view_proj[k])) return fail(c, AFR_ERR_INVALID_ARG, "afr_reproject_camera: matrix not finite");
+    if (!c->r_world) return fail(c, AFR_ERR_BAD_STATE, "afr_reproject_camera: context stores no world points");
+    afr::Camera cam;
+    for (int k = 0; k < 4; ++k) {
+        cam.m[k] = view_proj[k];           // row 0
+        cam.m[4 + k] = view_proj[4 + k];   // row 1
+        cam.m[8 + k] = view_proj[12 + k];  // row 3
+    }
+    cudaError_t e = afr::launch_reproject(c, t_now, &cam, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(c, e, "afr_reproject_camera");
+    c->frame_valid = true;
+    c->frame_t = t_now;
+    c->recon_valid = false;
+    return AFR_OK;
+}
+
 AfrStatus afr_reproject(AfrContext *c, float t_now, afr_stream_t stream) {
     if (!c) return AFR_ERR_INVALID_ARG;
     if (!std::isfinite(t_now)) return fail(c, AFR_ERR_INVALID_ARG, "afr_reproject: t_now not finite");
-    cudaError_t e = afr::launch_reproject(c, t_now, reinterpret_cast<cudaStream_t>(stream));
+    cudaError_t e = afr::launch_reproject(c, t_now, nullptr, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(c, e, "afr_reproject");
     c->frame_valid = true;
     c->frame_t = t_now;

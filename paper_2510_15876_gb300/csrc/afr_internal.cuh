@@ -35,6 +35,11 @@ struct TilePartial {
     double sgx, sgy, sgt;  // gradient sums over non-empty pixels
 };
 
+// Rows 0, 1 and 3 of a row-major view-projection matrix (camera reprojection).
+struct Camera {
+    float m[12];
+};
+
 // Per-context record of a batched launch (device memory).
 struct BatchCtx {
     int W, H, R, S, ntx, tbx, th, ntiles_x;
@@ -81,6 +86,8 @@ struct AfrContext {
     uint32_t *q_seq = nullptr;
     void *q_col = nullptr;
     uint32_t *q_total = nullptr;  // [1] accepted samples so far (the next slot is q_total mod N)
+    float4 *q_world = nullptr;    // [N] hit points (world_points contexts)
+    float4 *r_world = nullptr;    // [P*b] hit point of each queue slot (world_points contexts)
     uint32_t *fifo_flag = nullptr;  // [batch_cap] 1 for an accepted sample
     uint32_t *fifo_rank = nullptr;  // [batch_cap + 1] exclusive scan of fifo_flag, then the total
     uint32_t *fifo_scan = nullptr;  // scan block sums for batch_cap entries
@@ -229,7 +236,7 @@ cudaError_t launch_ingest(AfrContext *c, const AfrSampleBatch *batch, uint32_t n
                           cudaStream_t s);
 cudaError_t launch_fifo_append(AfrContext *c, const AfrSampleBatch *batch, uint32_t n, uint32_t seq0, cudaStream_t s);
 cudaError_t launch_gradients(AfrContext *c, float t_now, cudaStream_t s);
-cudaError_t launch_reproject(AfrContext *c, float t_now, cudaStream_t s);
+cudaError_t launch_reproject(AfrContext *c, float t_now, const Camera *cam, cudaStream_t s);
 cudaError_t launch_sigma(AfrContext *c, const AfrParams *prm, bool keep, bool adaptive, cudaStream_t s);
 cudaError_t launch_coverage_init(AfrContext *c, cudaStream_t s);
 cudaError_t launch_filter(AfrContext *c, float t_now, bool adaptive, float4 *out, cudaStream_t s);

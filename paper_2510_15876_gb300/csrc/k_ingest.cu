@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(32 * kPlaceWarps) k_place(const float4 *__rest
                                                             const float2 *__restrict__ mo, uint32_t n,
                                                             const uint2 *__restrict__ bin_of,
                                                             const uint32_t *__restrict__ poff,
+                                                            const float4 *__restrict__ world,
                                                             Rec64 *__restrict__ pk) {
     using CS = ColorStore<CT>;
     __shared__ uint4 stage[kPlaceWarps][32][5];
@@ -113,6 +114,10 @@ __global__ void __launch_bounds__(32 * kPlaceWarps) k_place(const float4 *__rest
                 d = __ldg(poff + bt.x) + bt.y;
                 Rec64 r;
                 RecCodec<CT>::pack(r, __ldg(pos + i), CS::raw(col, i), __ldg(mo + i), i);
+                if (world) {   // hit point in the record's spare 16 bytes
+                    const float4 w = __ldg(world + i);
+                    r.d = make_uint4(__float_as_uint(w.x), __float_as_uint(w.y), __float_as_uint(w.z), 0u);
+                }
                 stage[w][lane][0] = r.a;
                 stage[w][lane][1] = r.b;
                 stage[w][lane][2] = r.c;
@@ -169,7 +174,8 @@ __global__ void __launch_bounds__(256) k_commit(const uint32_t *__restrict__ pof
                                                 const Rec64 *__restrict__ pk, float2 *__restrict__ r_xy,
                                                 float2 *__restrict__ r_mo, float *__restrict__ r_t,
                                                 float *__restrict__ r_depth, uint32_t *__restrict__ r_seq,
-                                                void *__restrict__ r_col, uint32_t *__restrict__ r_state) {
+                                                void *__restrict__ r_col, uint32_t *__restrict__ r_state,
+                                                float4 *__restrict__ r_world) {
     using Codec = RecCodec<CT>;
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x >> 5);
@@ -206,6 +212,10 @@ __global__ void __launch_bounds__(256) k_commit(const uint32_t *__restrict__ pof
                 r_mo[dst] = Codec::motion(rec.b, rec.c);
                 r_seq[dst] = seq0 + i;
                 reinterpret_cast<typename Codec::T *>(r_col)[dst] = Codec::color(rec.b, rec.c);
+                if (r_world) {
+                    const uint4 d = __ldg(&pk[beg + lane].d);
+                    r_world[dst] = make_float4(__uint_as_float(d.x), __uint_as_float(d.y), __uint_as_float(d.z), 0.f);
+                }
             }
             continue;
         }
@@ -232,23 +242,28 @@ __global__ void __launch_bounds__(256) k_commit(const uint32_t *__restrict__ pof
             r_mo[dst] = Codec::motion(rb, rc);
             r_seq[dst] = seq0 + i;
             reinterpret_cast<typename Codec::T *>(r_col)[dst] = Codec::color(rb, rc);
+            if (r_world) {
+                const uint4 d = rec.d;
+                r_world[dst] = make_float4(__uint_as_float(d.x), __uint_as_float(d.y), __uint_as_float(d.z), 0.f);
+            }
         }
     }
 }
 
 template <int CT>
-cudaError_t run(AfrContext *c, const float4 *pos, const void *col, const float2 *mo, uint32_t n, uint32_t seq0,
-                cudaStream_t s) {
+cudaError_t run(AfrContext *c, const float4 *pos, const void *col, const float2 *mo, const float4 *world, uint32_t n,
+                uint32_t seq0, cudaStream_t s) {
     Rec64 *pk = reinterpret_cast<Rec64 *>(c->pack);
     cudaError_t e = cudaMemsetAsync(c->pcnt, 0, sizeof(uint32_t) * c->P, s);
     if (e != cudaSuccess) return e;
     const int g = grid_for(n, 256);
     k_hist<CT><<<g, 256, 0, s>>>(pos, col, mo, n, c->W, c->H, c->bin_of, c->pcnt, c->dcount);
     if ((e = scan_exclusive(c->pcnt, c->poff, c->P, c->scan_tmp, s)) != cudaSuccess) return e;
-    k_place<CT><<<grid_for(n, 32 * kPlaceWarps), 32 * kPlaceWarps, 0, s>>>(pos, col, mo, n, c->bin_of, c->poff, pk);
+    k_place<CT><<<grid_for(n, 32 * kPlaceWarps), 32 * kPlaceWarps, 0, s>>>(pos, col, mo, n, c->bin_of, c->poff,
+                                                                          c->r_world ? world : nullptr, pk);
     const int gc = grid_for((size_t)c->P * 32, 256);
     k_commit<CT><<<gc, 256, 0, s>>>(c->poff, c->P, c->b, seq0, pk, c->r_xy, c->r_mo, c->r_t, c->r_depth, c->r_seq,
-                                    c->r_col, c->r_state);
+                                    c->r_col, c->r_state, c->r_world);
     return cudaGetLastError();
 }
 
@@ -270,7 +285,8 @@ __global__ void __launch_bounds__(256) k_fifo_append(const float4 *__restrict__ 
                                                      const uint32_t *__restrict__ rank, uint32_t seq0, uint32_t N,
                                                      const uint32_t *__restrict__ total, float2 *__restrict__ q_xy,
                                                      float2 *__restrict__ q_mo, float *__restrict__ q_t,
-                                                     uint32_t *__restrict__ q_seq, void *__restrict__ q_col) {
+                                                     uint32_t *__restrict__ q_seq, void *__restrict__ q_col,
+                                                     const float4 *__restrict__ world, float4 *__restrict__ q_world) {
     using CS = ColorStore<CT>;
     const uint32_t accepted = rank[n - 1] + flag[n - 1], t0 = *total;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -282,6 +298,10 @@ __global__ void __launch_bounds__(256) k_fifo_append(const float4 *__restrict__ 
         q_mo[k] = __ldg(mo + i);
         q_seq[k] = seq0 + i;
         reinterpret_cast<typename CS::T *>(q_col)[k] = CS::raw(col, i);
+        if (q_world) {
+            const float4 w = __ldg(world + i);
+            q_world[k] = make_float4(w.x, w.y, w.z, 0.f);
+        }
     }
 }
 
@@ -291,14 +311,15 @@ __global__ void k_fifo_advance(const uint32_t *__restrict__ flag, const uint32_t
 }
 
 template <int CT>
-cudaError_t run_fifo(AfrContext *c, const float4 *pos, const void *col, const float2 *mo, uint32_t n, uint32_t seq0,
-                     cudaStream_t s) {
+cudaError_t run_fifo(AfrContext *c, const float4 *pos, const void *col, const float2 *mo, const float4 *world,
+                     uint32_t n, uint32_t seq0, cudaStream_t s) {
     const int g = grid_for(n, 256);
     k_fifo_flag<<<g, 256, 0, s>>>(c->bin_of, n, c->fifo_flag);
     cudaError_t e = scan_exclusive(c->fifo_flag, c->fifo_rank, n, c->fifo_scan, s);
     if (e != cudaSuccess) return e;
     k_fifo_append<CT><<<g, 256, 0, s>>>(pos, col, mo, n, c->fifo_flag, c->fifo_rank, seq0, (uint32_t)c->fifo_n,
-                                        c->q_total, c->q_xy, c->q_mo, c->q_t, c->q_seq, c->q_col);
+                                        c->q_total, c->q_xy, c->q_mo, c->q_t, c->q_seq, c->q_col, world,
+                                        c->q_world);
     k_fifo_advance<<<1, 1, 0, s>>>(c->fifo_flag, c->fifo_rank, n, c->q_total);
     return cudaGetLastError();
 }
@@ -309,10 +330,11 @@ cudaError_t launch_fifo_append(AfrContext *c, const AfrSampleBatch *batch, uint3
                                cudaStream_t s) {
     const float4 *pos = reinterpret_cast<const float4 *>(batch->pos_dev);
     const float2 *mo = reinterpret_cast<const float2 *>(batch->motion_dev);
+    const float4 *world = reinterpret_cast<const float4 *>(batch->world_dev);
     switch (c->ct) {
-        case AFR_F32: return run_fifo<AFR_F32>(c, pos, batch->color_dev, mo, n, seq0, s);
-        case AFR_F16: return run_fifo<AFR_F16>(c, pos, batch->color_dev, mo, n, seq0, s);
-        default: return run_fifo<AFR_BF16>(c, pos, batch->color_dev, mo, n, seq0, s);
+        case AFR_F32: return run_fifo<AFR_F32>(c, pos, batch->color_dev, mo, world, n, seq0, s);
+        case AFR_F16: return run_fifo<AFR_F16>(c, pos, batch->color_dev, mo, world, n, seq0, s);
+        default: return run_fifo<AFR_BF16>(c, pos, batch->color_dev, mo, world, n, seq0, s);
     }
 }
 
@@ -323,10 +345,11 @@ cudaError_t launch_ingest(AfrContext *c, const AfrSampleBatch *batch, uint32_t n
     const float4 *pos = reinterpret_cast<const float4 *>(batch->pos_dev);
     const float2 *mo = reinterpret_cast<const float2 *>(batch->motion_dev);
     const void *col = batch->color_dev;
+    const float4 *world = reinterpret_cast<const float4 *>(batch->world_dev);
     switch (c->ct) {
-        case AFR_F32: return run<AFR_F32>(c, pos, col, mo, n, seq0, s);
-        case AFR_F16: return run<AFR_F16>(c, pos, col, mo, n, seq0, s);
-        default: return run<AFR_BF16>(c, pos, col, mo, n, seq0, s);
+        case AFR_F32: return run<AFR_F32>(c, pos, col, mo, world, n, seq0, s);
+        case AFR_F16: return run<AFR_F16>(c, pos, col, mo, world, n, seq0, s);
+        default: return run<AFR_BF16>(c, pos, col, mo, world, n, seq0, s);
     }
 }
 

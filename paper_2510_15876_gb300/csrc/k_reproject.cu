@@ -34,6 +34,31 @@ __device__ __forceinline__ Moved move_sample(float2 xy, float2 m, float t, float
     return r;
 }
 
+// Section 6.2 with camera matrices: the stored hit point rendered by the
+// current camera, plus the sample's own screen motion times its age; each
+// matrix row summed left to right, one rounding per operation.
+__device__ __forceinline__ float cam_row(const Camera &c, int r, float4 w) {
+    float v = __fmul_rn(c.m[4 * r], w.x);
+    v = __fadd_rn(v, __fmul_rn(c.m[4 * r + 1], w.y));
+    v = __fadd_rn(v, __fmul_rn(c.m[4 * r + 2], w.z));
+    return __fadd_rn(v, c.m[4 * r + 3]);
+}
+
+__device__ __forceinline__ Moved move_camera(float4 w, float2 m, float t, float t_now, int W, int H,
+                                             const Camera &cam) {
+    Moved r;
+    const float cx = cam_row(cam, 0, w), cy = cam_row(cam, 1, w), cw = cam_row(cam, 2, w);
+    const float sx = __fmul_rn(__fadd_rn(__fmul_rn(__fdiv_rn(cx, cw), 0.5f), 0.5f), (float)W);
+    const float sy = __fmul_rn(__fadd_rn(__fmul_rn(__fdiv_rn(cy, cw), 0.5f), 0.5f), (float)H);
+    const float a = __fsub_rn(t_now, t);
+    r.xp = __fadd_rn(sx, __fmul_rn(m.x, a));
+    r.yp = __fadd_rn(sy, __fmul_rn(m.y, a));
+    r.a2 = __fmul_rn(a, a);
+    r.ok = cw > 0.f && r.xp >= 0.f && r.xp < (float)W && r.yp >= 0.f && r.yp < (float)H;
+    r.bin = r.ok ? (uint32_t)(int)floorf(r.yp) * (uint32_t)W + (uint32_t)(int)floorf(r.xp) : kInvalid;
+    return r;
+}
+
 // slot i -> (pixel, storage slot); b is a power of two in the common case
 __device__ __forceinline__ void split_slot(uint32_t i, int b, int bshift, uint32_t &p, int &s) {
     if (bshift >= 0) {
@@ -54,8 +79,9 @@ __device__ __forceinline__ bool slot_live(uint32_t st, int s, int b) {
 
 // FIFO: the slots are the reconstructor queue's, live below min(*state, nslots)
 // (state then points at its count of accepted samples).
-template <bool FIFO>
+template <bool FIFO, bool CAM>
 __global__ void __launch_bounds__(256) k_count(uint32_t nslots, int b, int bshift, int W, int H, float t_now,
+                                               Camera cam, const float4 *__restrict__ world,
                                                const uint32_t *__restrict__ state, const float2 *__restrict__ r_xy,
                                                const float2 *__restrict__ r_mo, const float *__restrict__ r_t,
                                                uint32_t *__restrict__ fcnt, uint32_t *__restrict__ amin2,
@@ -70,7 +96,8 @@ __global__ void __launch_bounds__(256) k_count(uint32_t nslots, int b, int bshif
             split_slot(i, b, bshift, p, s);
             if (!slot_live(__ldg(state + p), s, b)) continue;
         }
-        Moved mv = move_sample(__ldg(r_xy + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H);
+        Moved mv = CAM ? move_camera(__ldg(world + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H, cam)
+                       : move_sample(__ldg(r_xy + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H);
         agg_count(dcount + CNT_DROPPED, !mv.ok);
         if (!mv.ok) continue;
         agg_inc(fcnt, mv.bin);
@@ -81,8 +108,9 @@ __global__ void __launch_bounds__(256) k_count(uint32_t nslots, int b, int bshif
     }
 }
 
-template <int CT, bool FIFO>
+template <int CT, bool FIFO, bool CAM>
 __global__ void __launch_bounds__(256) k_scatter(uint32_t nslots, int b, int bshift, int W, int H, float t_now,
+                                                 Camera cam, const float4 *__restrict__ world,
                                                  const uint32_t *__restrict__ state, const float2 *__restrict__ r_xy,
                                                  const float2 *__restrict__ r_mo, const float *__restrict__ r_t,
                                                  const uint32_t *__restrict__ r_seq, const void *__restrict__ r_col,
@@ -100,7 +128,8 @@ __global__ void __launch_bounds__(256) k_scatter(uint32_t nslots, int b, int bsh
             split_slot(i, b, bshift, p, s);
             if (!slot_live(__ldg(state + p), s, b)) continue;
         }
-        Moved mv = move_sample(__ldg(r_xy + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H);
+        Moved mv = CAM ? move_camera(__ldg(world + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H, cam)
+                       : move_sample(__ldg(r_xy + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H);
         if (!mv.ok) continue;
         uint32_t e = __ldg(foff + mv.bin) + agg_inc(fcur, mv.bin);
         fpos[e] = make_float4(mv.xp, mv.yp, mv.a2, __int_as_float((int)floorf(mv.xp)));
@@ -147,28 +176,33 @@ __global__ void k_fill_u32(uint32_t *p, size_t n, uint32_t v) {
 
 }  // namespace
 
-cudaError_t launch_reproject(AfrContext *c, float t_now, cudaStream_t s) {
+cudaError_t launch_reproject(AfrContext *c, float t_now, const Camera *camp, cudaStream_t s) {
     cudaError_t e;
     if ((e = cudaMemsetAsync(c->fcnt, 0, sizeof(uint32_t) * c->P, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->dcount + CNT_DROPPED, 0, sizeof(unsigned long long) * 2, s)) != cudaSuccess) return e;
     k_fill_u32<<<grid_for(c->P, 256), 256, 0, s>>>(c->amin2, c->P, 0x7f800000u);
-    // source: the per-pixel queues, or the reconstructor queue (section 5.2)
-    const bool fifo = c->fifo_n > 0;
+    // source: the per-pixel queues, or the reconstructor queue (section 5.2);
+    // moved by screen motion, or rendered by a camera (hit points)
+    const bool fifo = c->fifo_n > 0, cam = camp != nullptr;
+    const Camera cm = cam ? *camp : Camera{};
     const size_t nsrc = fifo ? c->fifo_n : c->nslots;
     const uint32_t *state = fifo ? c->q_total : c->r_state;
     const float2 *xy = fifo ? c->q_xy : c->r_xy, *mo = fifo ? c->q_mo : c->r_mo;
     const float *tt = fifo ? c->q_t : c->r_t;
     const uint32_t *sq = fifo ? c->q_seq : c->r_seq;
     const void *col = fifo ? c->q_col : c->r_col;
+    const float4 *wp = fifo ? c->q_world : c->r_world;
     const int g = grid_for(nsrc, 256);
     const uint32_t ns = (uint32_t)nsrc;
     const int bshift = (c->b & (c->b - 1)) == 0 ? __builtin_ctz((unsigned)c->b) : -1;
-    if (fifo)
-        k_count<true><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, state, xy, mo, tt, c->fcnt, c->amin2,
-                                        c->dcount);
-    else
-        k_count<false><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, state, xy, mo, tt, c->fcnt, c->amin2,
-                                         c->dcount);
+#define AFR_COUNT(F_, C_)                                                                                    \
+    k_count<F_, C_><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, cm, wp, state, xy, mo, tt, c->fcnt, \
+                                      c->amin2, c->dcount)
+    if (fifo && cam) AFR_COUNT(true, true);
+    else if (fifo) AFR_COUNT(true, false);
+    else if (cam) AFR_COUNT(false, true);
+    else AFR_COUNT(false, false);
+#undef AFR_COUNT
     if ((e = scan_exclusive(c->fcnt, c->foff, c->P, c->scan_tmp, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->fcnt, 0, sizeof(uint32_t) * c->P, s)) != cudaSuccess) return e;
     // records land unordered in the second half of the buffers, then k_order
@@ -176,14 +210,15 @@ cudaError_t launch_reproject(AfrContext *c, float t_now, cudaStream_t s) {
     float4 *tmp_pos = c->fpos + c->frame_cap;
     void *tmp_col = static_cast<char *>(c->fcol) + c->frame_cap * c->csize;
     uint32_t *tmp_seq = c->fseq + c->frame_cap;
+#define AFR_SCATTER(CT_, F_, C_)                                                                              \
+    k_scatter<CT_, F_, C_><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, cm, wp, state, xy, mo, tt, sq, col, \
+                                             c->foff, c->fcnt, tmp_pos, tmp_col, tmp_seq)
 #define AFR_REPROJ(CT_)                                                                                        \
     do {                                                                                                       \
-        if (fifo)                                                                                              \
-            k_scatter<CT_, true><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, state, xy, mo, tt, sq, col, \
-                                                   c->foff, c->fcnt, tmp_pos, tmp_col, tmp_seq);              \
-        else                                                                                                   \
-            k_scatter<CT_, false><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, state, xy, mo, tt, sq,     \
-                                                    col, c->foff, c->fcnt, tmp_pos, tmp_col, tmp_seq);        \
+        if (fifo && cam) AFR_SCATTER(CT_, true, true);                                                         \
+        else if (fifo) AFR_SCATTER(CT_, true, false);                                                          \
+        else if (cam) AFR_SCATTER(CT_, false, true);                                                           \
+        else AFR_SCATTER(CT_, false, false);                                                                   \
         k_order<CT_><<<g, 256, 0, s>>>(c->W, c->foff, (uint32_t)c->P, tmp_pos, tmp_col, tmp_seq, c->fpos, c->fcol, \
                                        c->fseq, c->dcount);                                                    \
     } while (0)
@@ -193,6 +228,7 @@ cudaError_t launch_reproject(AfrContext *c, float t_now, cudaStream_t s) {
         default: AFR_REPROJ(AFR_BF16); break;
     }
 #undef AFR_REPROJ
+#undef AFR_SCATTER
     return cudaGetLastError();
 }
 
