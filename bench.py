@@ -274,7 +274,7 @@ def run_ours(args, rank, world):
     # adaptive footprints (section 6.2): successive reconstructions of the
     # same frame view, each sizing footprints from the previous one's coverage
     from paper_2510_15876_gb300 import _lib as L
-    adapt, tile_err = {}, {}
+    adapt, tile_err, camera = {}, {}, {}
     if not args.quick:
         _, pos, col, mo, out, tiles = keep
         step(rec, pos, col, mo, out, tiles)
@@ -309,6 +309,33 @@ def run_ours(args, rank, world):
             rec.tile_error(0.5, 0.5, 1.0)
         e4.record()
         torch.cuda.synchronize()
+        # camera-matrix reprojection (section 6.2) of the same batch with hit
+        # points, against the screen-motion reprojection
+        rec_w = Reconstructor(W, H, b, world_points=True, device=dev)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(0)
+        world = torch.rand((n, 4), generator=gen, device=dev) * torch.tensor([4.0, 4.0, 4.0, 0.0], device=dev) \
+            - torch.tensor([2.0, 2.0, -2.0, 0.0], device=dev)
+        rec_w.insert(pos, col, mo, world=world)
+        vp = np.array([[1.2, 0.1, 0.05, 0.02], [-0.05, 1.3, 0.1, -0.1], [0, 0, 1, 0], [0.01, 0.02, 0.4, 0.3]],
+                      np.float32)
+        cam_ms = {}
+        for name, fn in (("screen_motion", lambda: rec_w.reproject(T_NOW)),
+                         ("camera", lambda: rec_w.reproject_camera(T_NOW, vp))):
+            fn()
+            torch.cuda.synchronize()
+            s5, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s5.record()
+            for _ in range(args.steps):
+                fn()
+            e5.record()
+            torch.cuda.synchronize()
+            cam_ms[name] = round(s5.elapsed_time(e5) / args.steps, 4)
+        camera = {"reproject_ms": cam_ms, "frame_records": int(rec_w.query()["frame"]),
+                  "what": "1080p16 batch with random hit points in [-2, 2]^2 x [2, 6], perspective camera"}
+        rec_w.close()
+        del world
+        torch.cuda.empty_cache()
         tile_err = {"ms_per_call": round(s4.elapsed_time(e4) / args.steps, 4), "tiles": int(E.numel()),
                     "gain": {k: round(v, 6) for k, v in gain.items()},
                     "what": "afr_tile_error (kappa = lambda = 0.5, no occlusion data), including the device-to-host "
@@ -399,6 +426,7 @@ def run_ours(args, rank, world):
         "adaptive_footprint": adapt,
         "tile_error": tile_err,
         "fifo_vs_queue": fifo_cmp,
+        "camera_reprojection": camera,
         "batched": batched,
         "e2e": {"value": round(world * 1000.0 / e2e_ms, 3), "unit": "reconstructions/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4),
