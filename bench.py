@@ -314,9 +314,9 @@ def run_ours(args, rank, world):
         rec_w = Reconstructor(W, H, b, world_points=True, device=dev)
         gen = torch.Generator(device=dev)
         gen.manual_seed(0)
-        world = torch.rand((n, 4), generator=gen, device=dev) * torch.tensor([4.0, 4.0, 4.0, 0.0], device=dev) \
+        hits = torch.rand((n, 4), generator=gen, device=dev) * torch.tensor([4.0, 4.0, 4.0, 0.0], device=dev) \
             - torch.tensor([2.0, 2.0, -2.0, 0.0], device=dev)
-        rec_w.insert(pos, col, mo, world=world)
+        rec_w.insert(pos, col, mo, world=hits)
         vp = np.array([[1.2, 0.1, 0.05, 0.02], [-0.05, 1.3, 0.1, -0.1], [0, 0, 1, 0], [0.01, 0.02, 0.4, 0.3]],
                       np.float32)
         cam_ms = {}
@@ -334,7 +334,7 @@ def run_ours(args, rank, world):
         camera = {"reproject_ms": cam_ms, "frame_records": int(rec_w.query()["frame"]),
                   "what": "1080p16 batch with random hit points in [-2, 2]^2 x [2, 6], perspective camera"}
         rec_w.close()
-        del world
+        del hits
         torch.cuda.empty_cache()
         tile_err = {"ms_per_call": round(s4.elapsed_time(e4) / args.steps, 4), "tiles": int(E.numel()),
                     "gain": {k: round(v, 6) for k, v in gain.items()},
