@@ -439,6 +439,7 @@ def run_ours(args, rank, world):
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, batch, args.cpu_seconds)
+        line["cpu_baseline_all_cores"] = cpu_baseline_parallel(scene, batch)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -644,6 +645,26 @@ def cpu_baseline(scene, batch, budget_s):
             "sample": f"{k} runs of the whole oracle path (ingest, gradients, tile statistics, reprojection, "
                       f"widths, filter) on a {scene.width}x{band} band of the workload (its samples only), "
                       f"scaled by {H}/{band} rows"}
+
+
+def cpu_baseline_parallel(scene, batch, threads=None):
+    """The same oracle band step on every host core at once: one thread per
+    band (distinct bands of the image), the oracle's C routines releasing the
+    interpreter lock. Scaled to whole images by the rows covered."""
+    import concurrent.futures as cf
+    H = scene.height
+    band = 34
+    threads = threads or os.cpu_count() or 1
+    nb = min(threads, H // band)
+    y0s = [k * band for k in range(nb)]
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=nb) as ex:
+        list(ex.map(lambda y: _oracle_band_step(scene, batch, band, y), y0s))
+    wall = time.perf_counter() - t0
+    per_image = wall / (nb * band) * H
+    return {"value": round(1.0 / per_image, 6), "unit": "reconstructions/s", "cores": nb, "kind": "oracle",
+            "sample": f"{nb} bands of {scene.width}x{band} (rows 0..{nb * band}) in parallel threads, the whole "
+                      f"oracle path each, scaled by {H}/{nb * band} rows"}
 
 
 def run_reference(args, rank, world):
