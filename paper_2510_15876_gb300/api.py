@@ -135,12 +135,20 @@ class Reconstructor:
         self._check(self.lib.afr_tile_feedback(self.h, _ptr(out), _stream(stream)))
         return out
 
+    GAIN_KEYS = ("dC_ds", "dC_dt", "mean_age", "tile_width", "tile_count")
+
     def tile_error(self, kappa: float = 0.5, lam: float = 0.5, importance: float = 1.0,
-                   occluded: torch.Tensor | None = None, stream=None):
+                   occluded: torch.Tensor | None = None, stream=None, out=None, gain_on_device: bool = False):
         """Per-tile error E (sections 6.1) as a [n_tiles] float32 tensor and the
-        gain control (section 4.1) as a dict."""
-        E = torch.empty(self.n_tiles, dtype=torch.float32, device=self.device)
-        g = torch.empty(5, dtype=torch.float32, device=self.device)
+        gain control (section 4.1) as a dict; with gain_on_device, the gain
+        record stays on the device as a float32 tensor of the five
+        GAIN_KEYS values and nothing waits for the stream. out = (E, gain)
+        tensors to fill instead of new ones."""
+        if out is not None:
+            E, g = out
+        else:
+            E = torch.empty(self.n_tiles, dtype=torch.float32, device=self.device)
+            g = torch.empty(5, dtype=torch.float32, device=self.device)
         occ = None
         if occluded is not None:
             occ = occluded.to(self.device, torch.int32).contiguous()
@@ -148,8 +156,9 @@ class Reconstructor:
                 raise ValueError(f"occluded needs {self.n_tiles} counts")
         self._check(self.lib.afr_tile_error(self.h, kappa, lam, importance, _ptr(occ), _ptr(E), _ptr(g),
                                             _stream(stream)))
-        keys = ("dC_ds", "dC_dt", "mean_age", "tile_width", "tile_count")
-        return E, dict(zip(keys, g.cpu().tolist()))
+        if gain_on_device:
+            return E, g
+        return E, dict(zip(self.GAIN_KEYS, g.cpu().tolist()))
 
     def backward(self, grad_rgbw: torch.Tensor, want_colors: bool = True, want_params: bool = True,
                  n_frame: int | None = None, stream=None):

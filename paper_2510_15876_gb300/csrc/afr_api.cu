@@ -35,7 +35,7 @@ cudaError_t dalloc(T **p, size_t n) {
 void free_all(AfrContext *c) {
     void *ptrs[] = {c->r_xy, c->r_mo, c->r_t, c->r_depth, c->r_seq, c->r_col, c->r_state, c->bin_of,
                     c->pack,
-                    c->pcnt, c->poff, c->lbar, c->grad, c->pstat, c->sigma, c->tile_age, c->fconst, c->cov_r[0], c->cov_r[1], c->cov_n, c->amin2, c->tiles, c->fcnt,
+                    c->pcnt, c->poff, c->lbar, c->grad, c->pstat, c->sigma, c->tile_terms, c->fconst, c->cov_r[0], c->cov_r[1], c->cov_n, c->amin2, c->tiles, c->fcnt,
                     c->foff, c->fpos, c->fcol, c->fseq, c->q_xy, c->q_mo, c->q_t, c->q_seq, c->q_col, c->q_total, c->q_world, c->r_world, c->scan_tmp, c->bgrad, c->bparam, c->dcount, c->derr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -158,7 +158,7 @@ AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
     AFR_ALLOC(c->pstat, P);
     AFR_ALLOC(c->sigma, P);
     AFR_ALLOC(c->fconst, P);
-    AFR_ALLOC(c->tile_age, (size_t)c->ntiles);
+    AFR_ALLOC(c->tile_terms, (size_t)8 * c->ntiles);
     AFR_ALLOC(c->cov_r[0], P);
     AFR_ALLOC(c->cov_r[1], P);
     AFR_ALLOC(c->cov_n, P);

@@ -102,7 +102,7 @@ struct AfrContext {
     float4 *grad = nullptr;       // [P] (Gx, Gy, Gt, Lbar)
     float4 *pstat = nullptr;      // [P] (sum w, mean L, M2, Gt)
     float2 *sigma = nullptr;      // [P] (sigma_s, sigma_t)
-    double *tile_age = nullptr;   // [ntiles] sum of sample ages per tile (afr_tile_error)
+    double *tile_terms = nullptr;   // [8 ntiles] per-tile terms of afr_tile_error (64 B a tile)
     float4 *fconst = nullptr;     // [P] gather constants (-ks, -kt, exponent shift m, disc radius as int bits)
     float *cov_r[2] = {nullptr, nullptr};   // [P] footprint radii of adaptive reconstructions (ping-pong)
     int32_t *cov_n = nullptr;     // [P] samples in each pixel's footprint in the last adaptive reconstruction

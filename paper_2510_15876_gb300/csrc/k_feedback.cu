@@ -1,18 +1,24 @@
 // k_feedback.cu -- sections 4, 4.2 and 6.1: finalise the per-tile records
-// from the partials of the gradient pass. One block walks all tiles twice:
-// the mean number of empty slots over tiles (FP64), then each tile's record
-// with its undersampling measure u = 1 - min(1, m * mean_empty / empty).
+// from the partials of the gradient pass (the mean number of empty slots over
+// tiles in FP64, then each tile's record with its undersampling measure
+// u = 1 - min(1, m * mean_empty / empty)), and the tile error E with the gain
+// control of section 4.1.
 #include "afr_internal.cuh"
 
 namespace afr {
 namespace {
 
 constexpr int kFbThreads = 1024;
+constexpr int kFinThreads = 256;
 
-__global__ void __launch_bounds__(kFbThreads) k_finalize(int W, int H, int S, int ntx, int ntiles, int b, float m,
-                                                         const TilePartial *__restrict__ tiles,
-                                                         AfrTileStats *__restrict__ out) {
-    __shared__ double sh[kFbThreads / 32];
+// Every block sums the empty slots of all tiles (the same order in every
+// block, so the same FP64 mean), then writes the records of its own
+// kFinThreads tiles: the per-tile FP64 divisions spread over the SMs instead of
+// one block's FP64 pipe.
+__global__ void __launch_bounds__(kFinThreads) k_finalize(int W, int H, int S, int ntx, int ntiles, int b, float m,
+                                                          const TilePartial *__restrict__ tiles,
+                                                          AfrTileStats *__restrict__ out) {
+    __shared__ double sh[kFinThreads / 32];
     __shared__ double mean_empty;
     double acc = 0.0;
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
@@ -30,7 +36,8 @@ __global__ void __launch_bounds__(kFbThreads) k_finalize(int W, int H, int S, in
         mean_empty = s / ntiles;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ntiles) {
         int tx = t % ntx, ty = t / ntx;
         double A = (double)(min(S, W - tx * S) * min(S, H - ty * S));
         TilePartial tp = tiles[t];
@@ -49,110 +56,168 @@ __global__ void __launch_bounds__(kFbThreads) k_finalize(int W, int H, int S, in
     }
 }
 
-// Sum of sample ages max(0, t_now - t) over each tile's resident samples
-// (the queue's count newest slots of every pixel), one block per tile.
-__global__ void __launch_bounds__(256) k_tile_age(int W, int H, int S, int ntx, int b, float t_now,
-                                                  const uint32_t *__restrict__ state, const float *__restrict__ r_t,
-                                                  double *__restrict__ age_sum) {
+// Per-tile terms of the tile error, one block per tile: the sum of sample
+// ages max(0, t_now - t) over the tile's resident samples (the queue's count
+// newest slots of every pixel), then, by one thread, the tile's terms that do
+// not depend on other tiles. A tile row's slots are contiguous (tw pixels x b
+// slots): each thread keeps its slot columns and walks the rows, loading a
+// slot's time beside its pixel's queue state (a warp reads 128 contiguous
+// bytes of times) so that the loads of successive rows overlap. Ages are
+// summed in FP32 over at most 32 rows of one slot column (32 ages, each at
+// most the window) and in FP64 beyond: FP64 issues at 1/64 of the FP32 rate
+// on this part, too slow for a per-sample operation, and the tiles' FP64
+// divisions run here, spread over the SMs, rather than in the one block that
+// sums over tiles.
+struct alignas(64) TileTerm {
+    double v;           // luminance variance
+    double o;           // occluded share of the tile's slots
+    double inv_empty;   // 1 / empty slots (0 without empty slots)
+    double age;         // mean sample age (unused without samples)
+    double sg, sgt;     // spatial and temporal gradient sums over non-empty pixels
+    uint32_t empty, nonempty, has_samples, pad;
+};
+static_assert(sizeof(TileTerm) == 8 * sizeof(double), "eight doubles per tile");
+
+__global__ void __launch_bounds__(256) k_tile_terms(int W, int H, int S, int ntx, int b, float t_now,
+                                                    const uint32_t *__restrict__ state, const float *__restrict__ r_t,
+                                                    const TilePartial *__restrict__ tiles,
+                                                    const uint32_t *__restrict__ occluded,
+                                                    TileTerm *__restrict__ terms) {
     __shared__ double sh[8];
     const int tile = blockIdx.x;
     const int x0 = (tile % ntx) * S, y0 = (tile / ntx) * S;
     const int tw = min(S, W - x0), th = min(S, H - y0);
-    double acc = 0.0;
-    for (int k = threadIdx.x; k < tw * th; k += blockDim.x) {
-        const size_t p = (size_t)(y0 + k / tw) * W + x0 + k % tw;
-        const uint32_t st = state[p];
-        const int cnt = (int)(st & 0xFFFFu), head = (int)(st >> 16);
-        for (int j = 0; j < cnt; ++j) {
-            const int sl = ((head - 1 - j) % b + b) % b;
-            const double a = (double)t_now - (double)__ldg(r_t + p * b + sl);
-            acc += a > 0.0 ? a : 0.0;
+    const int row_slots = tw * b;
+    double d = 0.0;
+    for (int k = threadIdx.x; k < row_slots; k += blockDim.x) {
+        const int px = k / b, sl = k - px * b;
+        const size_t p0 = (size_t)y0 * W + x0 + px;
+        for (int r0 = 0; r0 < th; r0 += 32) {
+            const int r1 = min(th, r0 + 32);
+            float acc = 0.f;
+#pragma unroll 8
+            for (int r = r0; r < r1; ++r) {
+                const size_t p = p0 + (size_t)r * W;
+                const uint32_t st = __ldg(state + p);
+                const float t = __ldg(r_t + p * b + sl);
+                int age_rank = (int)(st >> 16) - 1 - sl;
+                if (age_rank < 0) age_rank += b;
+                const float a = t_now - t;
+                acc += (age_rank < (int)(st & 0xFFFFu) && a > 0.f) ? a : 0.f;
+            }
+            d += (double)acc;
         }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = d;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-        age_sum[tile] = t;
+        double age = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) age += sh[w];
+        const TilePartial tp = tiles[tile];
+        const double A = (double)(tw * th), empty = A * b - tp.n;
+        TileTerm tt;
+        tt.v = tp.sw > 0.0 ? tp.m2 / tp.sw : 0.0;
+        tt.o = occluded ? (double)occluded[tile] / (A * b) : 0.0;
+        tt.inv_empty = empty > 0.0 ? 1.0 / empty : 0.0;
+        tt.age = tp.n > 0.0 ? age / tp.n : 0.0;
+        tt.sg = 0.5 * (tp.sgx + tp.sgy);
+        tt.sgt = tp.sgt;
+        tt.empty = (uint32_t)empty;
+        tt.nonempty = (uint32_t)tp.nonempty;
+        tt.has_samples = tp.n > 0.0 ? 1u : 0u;
+        tt.pad = 0u;
+        terms[tile] = tt;
     }
 }
 
-template <int N>
-__device__ __forceinline__ void block_sum(double (&v)[N], double (*sh)[kFbThreads / 32]) {
+// Sum of each of N values over the block's kFbThreads threads: warp sums by
+// shuffles, then warp 0 sums the warps' partials and shares the totals (a
+// redundant per-thread sum over 32 partials would cost every warp 32 adds per
+// value, on the SM's narrow FP64 pipe for doubles).
+template <typename T, int N>
+__device__ __forceinline__ void block_sum(T (&v)[N], T (*sh)[kFbThreads / 32]) {
+    static_assert(kFbThreads == 1024, "warp 0 sums one partial per lane");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        double x = v[i];
+        T x = v[i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if ((threadIdx.x & 31) == 0) sh[i][threadIdx.x >> 5] = x;
+        if (lane == 0) sh[i][warp] = x;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            T x = sh[i][lane];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) sh[i][0] = x;
+        }
     }
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[i][w];
-        v[i] = t;
-    }
+    for (int i = 0; i < N; ++i) v[i] = sh[i][0];
     __syncthreads();
 }
 
-// Sections 6.1 and 4.1: tile error shares and gain control, one block.
-__global__ void __launch_bounds__(kFbThreads) k_tile_error(int W, int H, int S, int ntx, int ntiles, int b, float m,
+// Sections 6.1 and 4.1: tile error shares and gain control, one block over
+// the per-tile terms. The counts (empty slots, non-empty pixels, tiles with
+// samples) are summed as integers, exactly.
+__global__ void __launch_bounds__(kFbThreads) k_tile_error(int W, int H, int S, int ntx, int ntiles, float m,
                                                            double kappa, double lambda, double importance, double eps,
-                                                           const TilePartial *__restrict__ tiles,
-                                                           const double *__restrict__ age_sum,
-                                                           const uint32_t *__restrict__ occluded,
+                                                           const TileTerm *__restrict__ terms, bool has_occlusion,
                                                            float *__restrict__ E, AfrGain *__restrict__ gain) {
-    __shared__ double sh[8][kFbThreads / 32];
-    auto area = [&](int t) {
-        const int tx = t % ntx, ty = t / ntx;
-        return (double)(min(S, W - tx * S) * min(S, H - ty * S));
-    };
-    double e1[1] = {0.0};
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) e1[0] += area(t) * b - tiles[t].n;
-    block_sum(e1, sh);
-    const double mean_empty = e1[0] / ntiles;
-    auto var_u_o = [&](int t, double &v, double &u, double &o) {
-        const TilePartial tp = tiles[t];
-        const double A = area(t), empty = A * b - tp.n;
-        v = tp.sw > 0.0 ? tp.m2 / tp.sw : 0.0;
-        const double r = empty > 0.0 ? (double)m * mean_empty / empty : 0.0;
-        u = empty > 0.0 ? 1.0 - (r < 1.0 ? r : 1.0) : 0.0;
-        o = occluded ? (double)occluded[t] / (A * b) : 0.0;
-    };
-    // sums: v, u, o, spatial gradient, temporal gradient, non-empty pixels, tile mean ages, tiles with samples
-    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    __shared__ unsigned long long shi[3][kFbThreads / 32];
+    __shared__ double sh[6][kFbThreads / 32];
+    __shared__ double scal[4];   // m mean_empty, then the weights of v, u, o (one thread divides)
+    unsigned long long cnt[3] = {0ull, 0ull, 0ull};   // empty slots, non-empty pixels, tiles with samples
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-        double v, u, o;
-        var_u_o(t, v, u, o);
-        const TilePartial tp = tiles[t];
-        acc[0] += v;
-        acc[1] += u;
-        acc[2] += o;
-        acc[3] += 0.5 * (tp.sgx + tp.sgy);
-        acc[4] += tp.sgt;
-        acc[5] += tp.nonempty;
-        if (tp.n > 0.0) {
-            acc[6] += age_sum[t] / tp.n;
-            acc[7] += 1.0;
-        }
+        cnt[0] += terms[t].empty;
+        cnt[1] += terms[t].nonempty;
+        cnt[2] += terms[t].has_samples;
+    }
+    block_sum(cnt, shi);
+    if (threadIdx.x == 0) scal[0] = (double)m * ((double)cnt[0] / ntiles);
+    __syncthreads();
+    const double m_mean_empty = scal[0];
+    // u = 1 - min(1, m mean_empty / empty), 0 without empty slots
+    auto undersampling = [&](const TileTerm &tt) {
+        const double r = m_mean_empty * tt.inv_empty;
+        return tt.empty > 0u ? 1.0 - (r < 1.0 ? r : 1.0) : 0.0;
+    };
+    // sums: v, u, o, spatial gradient, temporal gradient, tile mean ages
+    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        const TileTerm tt = terms[t];
+        acc[0] += tt.v;
+        acc[1] += undersampling(tt);
+        acc[2] += tt.o;
+        acc[3] += tt.sg;
+        acc[4] += tt.sgt;
+        acc[5] += tt.has_samples ? tt.age : 0.0;
     }
     block_sum(acc, sh);
+    // E = s (kappa v / sum v + lambda u / sum u + (1 - kappa - lambda) o / sum o)
+    if (threadIdx.x == 0) {
+        scal[1] = acc[0] > 0.0 ? kappa / acc[0] : 0.0;
+        scal[2] = acc[1] > 0.0 ? lambda / acc[1] : 0.0;
+        scal[3] = has_occlusion && acc[2] > 0.0 ? (1.0 - kappa - lambda) / acc[2] : 0.0;
+    }
+    __syncthreads();
+    const double wv = scal[1], wu = scal[2], wo = scal[3];
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-        double v, u, o;
-        var_u_o(t, v, u, o);
-        double e = 0.0;
-        if (acc[0] > 0.0) e += kappa * v / acc[0];
-        if (acc[1] > 0.0) e += lambda * u / acc[1];
-        if (occluded && acc[2] > 0.0) e += (1.0 - kappa - lambda) * o / acc[2];
-        E[t] = (float)(area(t) * e);
+        const TileTerm tt = terms[t];
+        const int tx = t % ntx, ty = t / ntx;
+        const double A = (double)(min(S, W - tx * S) * min(S, H - ty * S));
+        E[t] = (float)(A * (wv * tt.v + wu * undersampling(tt) + wo * tt.o));
     }
     if (threadIdx.x == 0 && gain) {
-        const double dcds = acc[5] > 0.0 ? acc[3] / acc[5] : 0.0, dcdt = acc[5] > 0.0 ? acc[4] / acc[5] : 0.0;
-        const double T = acc[7] > 0.0 ? acc[6] / acc[7] : 0.0;
+        const double nonempty = (double)cnt[1];
+        const double dcds = nonempty > 0.0 ? acc[3] / nonempty : 0.0, dcdt = nonempty > 0.0 ? acc[4] / nonempty : 0.0;
+        const double T = cnt[2] > 0ull ? acc[5] / (double)cnt[2] : 0.0;
         const double Sw = importance * dcdt * T / (dcds > eps ? dcds : eps);
         const double P = (double)W * H;
         double N = Sw > 0.0 ? P / (Sw * Sw) : P;
@@ -171,17 +236,17 @@ __global__ void __launch_bounds__(kFbThreads) k_tile_error(int W, int H, int S, 
 
 cudaError_t launch_tile_error(AfrContext *c, float kappa, float lambda, float importance, const uint32_t *occluded,
                               float *E, AfrGain *gain, cudaStream_t s) {
-    k_tile_age<<<c->ntiles, 256, 0, s>>>(c->W, c->H, c->S, c->ntx, c->b, c->grads_t, c->r_state, c->r_t,
-                                         c->tile_age);
-    k_tile_error<<<1, kFbThreads, 0, s>>>(c->W, c->H, c->S, c->ntx, c->ntiles, c->b, c->cfg.undersample_m, kappa,
-                                          lambda, importance, c->cfg.eps_grad, c->tiles, c->tile_age, occluded, E,
-                                          gain);
+    TileTerm *terms = reinterpret_cast<TileTerm *>(c->tile_terms);
+    k_tile_terms<<<c->ntiles, 256, 0, s>>>(c->W, c->H, c->S, c->ntx, c->b, c->grads_t, c->r_state, c->r_t, c->tiles,
+                                           occluded, terms);
+    k_tile_error<<<1, kFbThreads, 0, s>>>(c->W, c->H, c->S, c->ntx, c->ntiles, c->cfg.undersample_m, kappa, lambda,
+                                          importance, c->cfg.eps_grad, terms, occluded != nullptr, E, gain);
     return cudaGetLastError();
 }
 
 cudaError_t launch_feedback(AfrContext *c, AfrTileStats *out, cudaStream_t s) {
-    k_finalize<<<1, kFbThreads, 0, s>>>(c->W, c->H, c->S, c->ntx, c->ntiles, c->b, c->cfg.undersample_m, c->tiles,
-                                        out);
+    k_finalize<<<(c->ntiles + kFinThreads - 1) / kFinThreads, kFinThreads, 0, s>>>(
+        c->W, c->H, c->S, c->ntx, c->ntiles, c->b, c->cfg.undersample_m, c->tiles, out);
     return cudaGetLastError();
 }
 

@@ -39,7 +39,7 @@ def _setup(dev, W, H, b, S, seed):
     return rec, ring
 
 
-@pytest.mark.parametrize("W,H,b,S", [(160, 96, 8, 32), (131, 67, 4, 16)])
+@pytest.mark.parametrize("W,H,b,S", [(160, 96, 8, 32), (131, 67, 4, 16), (300, 140, 16, 64)])
 @pytest.mark.parametrize("with_occlusion", [False, True])
 def test_tile_error_and_gain_match_oracle(dev, W, H, b, S, with_occlusion):
     rec, ring = _setup(dev, W, H, b, S, seed=W)
@@ -65,3 +65,13 @@ def test_tile_error_rejects_bad_weights(dev):
         with pytest.raises(L.AfrError) as ei:
             rec.tile_error(kappa, lam, imp)
         assert ei.value.status == L.AFR_ERR_INVALID_ARG
+
+
+def test_gain_on_device_and_preallocated_outputs(dev):
+    rec, _ = _setup(dev, 131, 67, 4, 16, seed=9)
+    E, gain = rec.tile_error(0.3, 0.3, 2.0)
+    out = (torch.full_like(E, -1.0), torch.full((5,), -1.0, device=dev))
+    E2, g2 = rec.tile_error(0.3, 0.3, 2.0, out=out, gain_on_device=True)
+    assert E2.data_ptr() == out[0].data_ptr() and g2.data_ptr() == out[1].data_ptr()
+    assert torch.equal(E, E2)
+    assert g2.cpu().tolist() == [gain[k] for k in rec.GAIN_KEYS]
