@@ -192,7 +192,8 @@ def test_full_size_sampled_parity(dev):
     """1920x1080x16 (33,177,600 samples), the benchmark's launch sequence:
     queues, frame bins and tile counts bit-exact everywhere; widths and colours
     against the oracle at 4096 sampled pixels, each stage on the oracle's
-    own input to it."""
+    own input to it; then the tile error over every tile and four images with
+    adaptive footprints (radii and coverage counts bit-exact everywhere)."""
     from paper_2510_15876_gb300.api import Reconstructor, to_device_batch, decode_tiles
     scene, batch = scenes.config_stream("c3_1920x1080x16", 0)
     W, H, b = scene.width, scene.height, scene.spec.depth
@@ -239,4 +240,28 @@ def test_full_size_sampled_parity(dev):
     full = oracle.reconstruct(ring, pixels=pix)["image"][pix]
     e2e = np.abs(img[pix, :3] - full[:, :3]) / np.maximum(np.abs(full[:, :3]), 1e-3)
     assert np.quantile(e2e, 0.99) < 1e-4, np.quantile(e2e, 0.99)
+    # tile error and gain control (sections 6.1, 4.1) over all 2040 tiles
+    E, gain = rec.tile_error(0.35, 0.4, 1.25)
+    E_ref, g_ref = oracle.tile_error(ring, wt, 32, T_NOW, None, 0.35, 0.4, 1.25)
+    np.testing.assert_allclose(E.cpu().numpy().astype(np.float64), E_ref, rtol=1e-4, atol=1e-5 * np.abs(E_ref).max())
+    np.testing.assert_allclose([gain[k] for k in rec.GAIN_KEYS], g_ref, rtol=1e-4)
+    # adaptive footprints (section 6.2), four images on the oracle's widths:
+    # radii and coverage counts bit-exact everywhere, colours at the samples
+    state_r, state_n = np.full(W * H, 4.0, np.float32), np.full(W * H, -1, np.int32)
+    seen = set()
+    for frame in range(4):
+        flags = L.AFR_RECON_KEEP_SIGMA | L.AFR_RECON_ADAPTIVE_SUPPORT | (L.AFR_RECON_COVERAGE_RESET if frame == 0 else 0)
+        got = rec.reconstruct(T_NOW, flags=flags).cpu().numpy().reshape(-1, 4)[pix].astype(np.float64)
+        state_r, R_ref = oracle.coverage_update(W, H, state_r, state_n)
+        state_n = oracle.coverage_count(W, H, R_ref, woff)
+        assert np.array_equal(rec.export_map(L.AFR_MAP_FOOTPRINT), state_r)
+        assert np.array_equal(rec.export_map(L.AFR_MAP_COVERAGE).astype(np.int64), state_n)
+        ref = oracle.filter_image(W, H, woff, wrec, ss32.astype(np.float64), st32.astype(np.float64), R=R_ref,
+                                  pixels=pix)[pix]
+        hole = ref[:, 3] == 0
+        assert np.all(got[hole] == 0)
+        err = np.abs(got[~hole, :3] - ref[~hole, :3]) / np.maximum(np.abs(ref[~hole, :3]), 1e-3)
+        assert err.max() <= 1e-5, (frame, err.max())
+        seen.update(np.unique(R_ref).tolist())
+    assert len(seen) >= 3          # the footprints did change across images
     rec.close()
