@@ -23,6 +23,18 @@
  *    CUDA device is usable, afr_create returns AFR_ERR_CUDA.
  *  - Calls on one context are not thread-safe; distinct contexts are
  *    independent.
+ *  - After afr_insert_samples, afr_estimate_gradients (with the
+ *    afr_tile_feedback and afr_tile_error that read its tile statistics) and
+ *    afr_reproject or afr_reproject_camera read the sample buffers and write
+ *    disjoint state, so the two branches may be issued on two streams and run
+ *    concurrently; afr_reconstruct reads both branches' results and must be
+ *    ordered after both (for instance with an event recorded on the other
+ *    stream). afr_reconstruct reads neither the sample buffers nor the ingest
+ *    scratch, so the next afr_reset and afr_insert_samples may run on another
+ *    stream concurrently with it, once both branches have finished; the next
+ *    afr_estimate_gradients and afr_reproject must again follow it. (The call
+ *    order checks are made when a call is issued: issue afr_reconstruct before
+ *    the next afr_insert_samples.)
  */
 #ifndef AFR_H
 #define AFR_H

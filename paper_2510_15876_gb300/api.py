@@ -61,6 +61,8 @@ class Reconstructor:
         n = ctypes.c_uint32()
         self._check(self.lib.afr_num_tiles(self.h, ctypes.byref(n)))
         self.n_tiles = n.value
+        self._side = None                 # refresh(): stream of the gradient branch
+        self._fork, self._join = torch.cuda.Event(), torch.cuda.Event()
 
     # -- plumbing ------------------------------------------------------------------
     def _check(self, st: int):
@@ -134,6 +136,39 @@ class Reconstructor:
             out = torch.empty((self.n_tiles, 8), dtype=torch.float32, device=self.device)
         self._check(self.lib.afr_tile_feedback(self.h, _ptr(out), _stream(stream)))
         return out
+
+    def refresh(self, t_now: float = 1.0, out: torch.Tensor | None = None, tiles: torch.Tensor | None = None,
+                params=None, flags: int = 0, stream=None, side_stream=None, reads_done=None):
+        """One displayed image from the buffered samples: the gradients
+        (sections 4, 4.1) and the tile statistics (sections 4.2, 6.1) on
+        side_stream while the samples are reprojected (section 6.2) on
+        stream, then the widths and the filter (sections 5.1, 5.2) on stream
+        once both are done. The two branches read the sample buffers and
+        write disjoint state. reads_done (a torch.cuda.Event), if given, is
+        recorded on stream when both branches are done with the sample
+        buffers, before the filter: an insert of the next batch on another
+        stream that waits for it overlaps the filter (the filter reads no
+        sample buffer). Returns (image, tile statistics)."""
+        main = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if side_stream is None:
+            if self._side is None:
+                self._side = torch.cuda.Stream(self.device, priority=-1)
+            side_stream = self._side
+        if tiles is None:
+            tiles = torch.empty((self.n_tiles, 8), dtype=torch.float32, device=self.device)
+        if out is None:
+            out = torch.empty((self.H, self.W, 4), dtype=torch.float32, device=self.device)
+        self._fork.record(main)
+        side_stream.wait_event(self._fork)
+        self.estimate_gradients(t_now, stream=side_stream)
+        self.tile_feedback(out=tiles, stream=side_stream)
+        self._join.record(side_stream)
+        self.reproject(t_now, stream=main)
+        main.wait_event(self._join)
+        if reads_done is not None:
+            reads_done.record(main)
+        self.reconstruct(t_now, params, out, flags, stream=main)
+        return out, tiles
 
     GAIN_KEYS = ("dC_ds", "dC_dt", "mean_age", "tile_width", "tile_count")
 

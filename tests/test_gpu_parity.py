@@ -325,6 +325,62 @@ def test_call_order_is_enforced(dev):
     assert rec.status() == L.AFR_OK
 
 
+@pytest.mark.parametrize("W,H,b", [(96, 80, 4), (640, 360, 8)])
+def test_refresh_matches_serial_calls(dev, W, H, b):
+    """refresh() runs the gradient branch on a side stream beside the
+    reprojection: the same image and tile statistics, bit for bit, as the
+    calls in series, over several refreshes of a changing buffer."""
+    sc, batch = _scene_batch("c4_512x512x8", seed=3, n=W * H * b, W=W, H=H, b=b)
+    a, s = _mk(dev, W, H, b), _mk(dev, W, H, b)
+    cuts = np.linspace(0, len(batch["pos"]), 4).astype(int)
+    for i, (lo, hi) in enumerate(zip(cuts[:-1], cuts[1:])):
+        part = {k: np.ascontiguousarray(v[lo:hi]) for k, v in batch.items()}
+        _upload(a, part)
+        _upload(s, part)
+        t = T_NOW - 0.1 * (2 - i)
+        img_a, tiles_a = a.refresh(t)
+        s.estimate_gradients(t)
+        s.reproject(t)
+        img_s = s.reconstruct(t)
+        tiles_s = s.tile_feedback()
+        assert torch.equal(img_a, img_s) and torch.equal(tiles_a, tiles_s)
+    assert a.query() == s.query()
+
+
+def test_pipelined_steps_match_serial(dev):
+    """The next batch's reset and insert on another stream, waiting only for
+    refresh()'s reads_done event, overlap the current image's filter: every
+    image and tile record equals the one from calls in series."""
+    from paper_2510_15876_gb300.api import to_device_batch
+    W, H, b = 640, 360, 8
+    batches = []
+    for seed in range(4):
+        _, bt = _scene_batch("c4_512x512x8", seed=seed, n=W * H * b, W=W, H=H, b=b, speed=24.0 + 8 * seed)
+        batches.append(to_device_batch(bt, dev))
+    a, s = _mk(dev, W, H, b), _mk(dev, W, H, b)
+    want = []
+    for pos, col, mo in batches:
+        s.reset()
+        s.insert(pos, col, mo)
+        s.estimate_gradients(T_NOW)
+        s.reproject(T_NOW)
+        want.append((s.reconstruct(T_NOW), s.tile_feedback()))
+    main, ingest = torch.cuda.current_stream(), torch.cuda.Stream(dev)
+    reads_done, ingested = torch.cuda.Event(), torch.cuda.Event()
+    reads_done.record(main)
+    got = []
+    for pos, col, mo in batches:
+        ingest.wait_event(reads_done)
+        a.reset(stream=ingest)
+        a.insert(pos, col, mo, stream=ingest)
+        ingested.record(ingest)
+        main.wait_event(ingested)
+        got.append(a.refresh(T_NOW, reads_done=reads_done))
+    torch.cuda.synchronize()
+    for (img, tiles), (img_w, tiles_w) in zip(got, want):
+        assert torch.equal(img, img_w) and torch.equal(tiles, tiles_w)
+
+
 # ----------------------------------------------------------------------------- end to end
 @pytest.mark.parametrize("key", ["c1_128x128x4"])
 def test_end_to_end_c1(dev, key):
