@@ -199,18 +199,35 @@ __device__ __forceinline__ float ex2(float x) {
     return y;
 }
 
+// Rounds of key grouping before the remaining lanes fall back to one atomic
+// each: each round takes the lowest pending lane's key and ballots the lanes
+// that share it (a shuffle and a ballot, far cheaper here than a
+// __match_any_sync); samples moving together give a warp a few distinct keys,
+// while keys spread at random are left to per-lane atomics after the rounds.
+constexpr int kGroupRounds = 4;
+
 // Warp-aggregated atomic add of 1 at base[key]: lanes with equal keys share
-// one atomic; returns this lane's ticket.
+// one atomic (up to kGroupRounds keys a warp); returns this lane's ticket.
+// Tickets of one key are distinct and dense; their order is unspecified.
 __device__ __forceinline__ uint32_t agg_inc(uint32_t *base, uint32_t key) {
-    unsigned mask = __activemask();
-    unsigned peers = __match_any_sync(mask, key);
-    int lane = threadIdx.x & 31;
-    int leader = __ffs(peers) - 1;
-    uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+    const unsigned active = __activemask();
+    const int lane = threadIdx.x & 31;
+    unsigned todo = active, mine = 0u;
+    int my_leader = lane;
     uint32_t first = 0;
-    if (lane == leader) first = atomicAdd(base + key, (uint32_t)__popc(peers));
-    first = __shfl_sync(peers, first, leader);
-    return first + rank;
+    for (int round = 0; round < kGroupRounds && todo; ++round) {
+        const int leader = __ffs(todo) - 1;
+        const uint32_t k = __shfl_sync(active, key, leader);
+        const unsigned peers = __ballot_sync(active, key == k);
+        if (lane == leader) first = atomicAdd(base + k, (uint32_t)__popc(peers));
+        if (key == k) {
+            mine = peers;
+            my_leader = leader;
+        }
+        todo &= ~peers;
+    }
+    if (todo & (1u << lane)) return atomicAdd(base + key, 1u);
+    return __shfl_sync(active & ~todo, first, my_leader) + __popc(mine & ((1u << lane) - 1u));
 }
 
 // Warp-aggregated count of lanes with flag set, added to *ctr.

@@ -100,11 +100,29 @@ __global__ void __launch_bounds__(256) k_count(uint32_t nslots, int b, int bshif
                        : move_sample(__ldg(r_xy + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H);
         agg_count(dcount + CNT_DROPPED, !mv.ok);
         if (!mv.ok) continue;
-        agg_inc(fcnt, mv.bin);
-        unsigned mask = __activemask();
-        unsigned peers = __match_any_sync(mask, mv.bin);
-        uint32_t bits = __reduce_min_sync(peers, __float_as_uint(mv.a2));   // a^2 >= 0: bit order = value order
-        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicMin(amin2 + mv.bin, bits);
+        // lanes sharing a bin add their count and their smallest a^2 through
+        // the lowest of them (a^2 >= 0: bit order = value order); after
+        // kGroupRounds bins the remaining lanes add their own
+        const unsigned active = __activemask();
+        const int lane = threadIdx.x & 31;
+        const uint32_t a2bits = __float_as_uint(mv.a2);
+        unsigned todo = active;
+        for (int round = 0; round < kGroupRounds && todo; ++round) {
+            const int leader = __ffs(todo) - 1;
+            const uint32_t k = __shfl_sync(active, mv.bin, leader);
+            const bool in = mv.bin == k;
+            const unsigned peers = __ballot_sync(active, in);
+            const uint32_t bits = __reduce_min_sync(active, in ? a2bits : 0xFFFFFFFFu);
+            if (lane == leader) {
+                atomicAdd(fcnt + k, (uint32_t)__popc(peers));
+                atomicMin(amin2 + k, bits);
+            }
+            todo &= ~peers;
+        }
+        if (todo & (1u << lane)) {
+            atomicAdd(fcnt + mv.bin, 1u);
+            atomicMin(amin2 + mv.bin, a2bits);
+        }
     }
 }
 
