@@ -319,7 +319,7 @@ AFR_API AfrStatus afr_reconstruct_ex(AfrContext *ctx, float t_now, const AfrPara
 
 /* Filter tuning of a context: footprint radius R (0..8; it changes results:
  * the footprint is the integer disc of radius R) and the filter's CTA tile,
- * (2*tile_bx) x (64/tile_bx) pixels with tile_bx in {2, 4, 8, 16} (default 8;
+ * (2*tile_bx) x (64/tile_bx) pixels with tile_bx in {2, 4, 8, 16} (default 4;
  * it does not change results). */
 AFR_API AfrStatus afr_set_tuning(AfrContext *ctx, int32_t radius, int32_t tile_bx);
 

@@ -142,7 +142,7 @@ struct AfrContext {
     float recon_t = 0.f;
     AfrParams recon_params{};
     bool sigma_imported = false;
-    int tile_bx = 8;              // filter CTA tile: (2*tile_bx) x (64/tile_bx) pixels
+    int tile_bx = 4;              // filter CTA tile: (2*tile_bx) x (64/tile_bx) pixels (8 x 16 measured fastest at 1080p16)
     // filter kernel timing (afr_profile_filter): event pairs, launches recorded
     cudaEvent_t *prof_ev = nullptr;
     bool prof_on = false, prof_capture_hit = false;
