@@ -138,7 +138,7 @@ class Reconstructor:
         return out
 
     def refresh(self, t_now: float = 1.0, out: torch.Tensor | None = None, tiles: torch.Tensor | None = None,
-                params=None, flags: int = 0, stream=None, side_stream=None, reads_done=None):
+                params=None, flags: int = 0, stream=None, side_stream=None, reads_done=None, view_proj=None):
         """One displayed image from the buffered samples: the gradients
         (sections 4, 4.1) and the tile statistics (sections 4.2, 6.1) on
         side_stream while the samples are reprojected (section 6.2) on
@@ -148,7 +148,9 @@ class Reconstructor:
         recorded on stream when both branches are done with the sample
         buffers, before the filter: an insert of the next batch on another
         stream that waits for it overlaps the filter (the filter reads no
-        sample buffer). Returns (image, tile statistics)."""
+        sample buffer). view_proj, if given, reprojects the stored hit points
+        with that camera (reproject_camera) instead of the screen motion.
+        Returns (image, tile statistics)."""
         main = stream if stream is not None else torch.cuda.current_stream(self.device)
         if side_stream is None:
             if self._side is None:
@@ -163,7 +165,10 @@ class Reconstructor:
         self.estimate_gradients(t_now, stream=side_stream)
         self.tile_feedback(out=tiles, stream=side_stream)
         self._join.record(side_stream)
-        self.reproject(t_now, stream=main)
+        if view_proj is None:
+            self.reproject(t_now, stream=main)
+        else:
+            self.reproject_camera(t_now, view_proj, stream=main)
         main.wait_event(self._join)
         if reads_done is not None:
             reads_done.record(main)

@@ -103,6 +103,21 @@ def test_camera_filter_matches_oracle(dev):
     assert err.max() <= 1e-5, err.max()
 
 
+def test_camera_refresh_matches_serial_calls(dev):
+    """refresh(view_proj=...) with the gradient branch on its side stream: the
+    same image and tile statistics as the calls in series."""
+    W, H, b = 96, 80, 4
+    a, _, _ = _make(dev, W, H, b, seed=5)
+    s, _, _ = _make(dev, W, H, b, seed=5)
+    img_a, tiles_a = a.refresh(T_NOW, view_proj=VP)
+    s.estimate_gradients(T_NOW)
+    s.reproject_camera(T_NOW, VP)
+    img_s = s.reconstruct(T_NOW)
+    tiles_s = s.tile_feedback()
+    assert torch.equal(img_a, img_s) and torch.equal(tiles_a, tiles_s)
+    assert a.query()["frame"] == s.query()["frame"] > 0
+
+
 def test_camera_argument_checks(dev):
     from paper_2510_15876_gb300.api import Reconstructor, to_device_batch
     batch = _stream(32, 24, 4, 7)
