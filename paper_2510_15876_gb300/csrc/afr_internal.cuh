@@ -25,15 +25,19 @@ enum { CNT_REJECTED = 0, CNT_DROPPED, CNT_UNSORTED, CNT_RESIDENT, CNT_BIG, CNT_N
 // device status word bits
 enum { ERR_TIMEOUT = 1u, ERR_CHECK = 2u };
 
-// Per-tile partial statistics written by the gradient pass.
-struct TilePartial {
-    double n;          // samples
-    double nonempty;   // non-empty pixels
+// Per-tile partial statistics written by the gradient pass (64 bytes). The
+// luminance moments are FP64 because a tile above 4096 samples merges its
+// warps' moments in FP64; everything else is an integer count or an FP32 sum.
+struct alignas(16) TilePartial {
     double sw;         // sum of age weights
     double mean;       // weighted mean luminance
     double m2;         // weighted sum of squared deviations
-    double sgx, sgy, sgt;  // gradient sums over non-empty pixels
+    float sgx, sgy, sgt;   // gradient sums over non-empty pixels
+    uint32_t n;        // samples
+    uint32_t nonempty; // non-empty pixels
+    uint32_t pad[3];
 };
+static_assert(sizeof(TilePartial) == 64, "one 64-byte record per tile");
 
 // Rows 0, 1 and 3 of a row-major view-projection matrix (camera reprojection).
 struct Camera {

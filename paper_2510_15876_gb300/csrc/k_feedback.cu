@@ -1,8 +1,10 @@
 // k_feedback.cu -- sections 4, 4.2 and 6.1: finalise the per-tile records
 // from the partials of the gradient pass (the mean number of empty slots over
-// tiles in FP64, then each tile's record with its undersampling measure
+// tiles, then each tile's record with its undersampling measure
 // u = 1 - min(1, m * mean_empty / empty)), and the tile error E with the gain
-// control of section 4.1.
+// control of section 4.1. Counts are summed as integers and the rest runs in
+// FP32: FP64 issues at 1/64 of the FP32 rate on this part, and every output
+// is FP32.
 #include "afr_internal.cuh"
 
 namespace afr {
@@ -11,47 +13,46 @@ namespace {
 constexpr int kFbThreads = 1024;
 constexpr int kFinThreads = 256;
 
-// Every block sums the empty slots of all tiles (the same order in every
-// block, so the same FP64 mean), then writes the records of its own
-// kFinThreads tiles: the per-tile FP64 divisions spread over the SMs instead of
-// one block's FP64 pipe.
+__device__ __forceinline__ uint32_t tile_area(int t, int W, int H, int S, int ntx) {
+    const int tx = t % ntx, ty = t / ntx;
+    return (uint32_t)(min(S, W - tx * S) * min(S, H - ty * S));
+}
+
+// Every block sums the empty slots of all tiles (an exact integer sum, the
+// same in every block), then writes the records of its own kFinThreads tiles.
 __global__ void __launch_bounds__(kFinThreads) k_finalize(int W, int H, int S, int ntx, int ntiles, int b, float m,
                                                           const TilePartial *__restrict__ tiles,
                                                           AfrTileStats *__restrict__ out) {
-    __shared__ double sh[kFinThreads / 32];
-    __shared__ double mean_empty;
-    double acc = 0.0;
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-        int tx = t % ntx, ty = t / ntx;
-        double A = (double)(min(S, W - tx * S) * min(S, H - ty * S));
-        acc += A * b - tiles[t].n;
-    }
+    __shared__ unsigned long long sh[kFinThreads / 32];
+    __shared__ float mean_empty;
+    unsigned long long acc = 0ull;
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
+        acc += (unsigned long long)tile_area(t, W, H, S, ntx) * (uint32_t)b - tiles[t].n;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
+        unsigned long long s = 0ull;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-        mean_empty = s / ntiles;
+        mean_empty = (float)s / (float)ntiles;
     }
     __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < ntiles) {
-        int tx = t % ntx, ty = t / ntx;
-        double A = (double)(min(S, W - tx * S) * min(S, H - ty * S));
-        TilePartial tp = tiles[t];
-        double empty = A * b - tp.n;
+        const TilePartial tp = tiles[t];
+        const uint32_t empty = tile_area(t, W, H, S, ntx) * (uint32_t)b - tp.n;
+        const float sw = (float)tp.sw, ne = (float)tp.nonempty;
         AfrTileStats o;
-        o.n = (uint32_t)tp.n;
-        o.empty_slots = (uint32_t)empty;
-        o.mean_L = tp.sw > 0.0 ? (float)tp.mean : 0.f;
-        o.var_L = tp.sw > 0.0 ? (float)(tp.m2 / tp.sw) : 0.f;
-        o.mean_Gx = tp.nonempty > 0.0 ? (float)(tp.sgx / tp.nonempty) : 0.f;
-        o.mean_Gy = tp.nonempty > 0.0 ? (float)(tp.sgy / tp.nonempty) : 0.f;
-        o.mean_Gt = tp.nonempty > 0.0 ? (float)(tp.sgt / tp.nonempty) : 0.f;
-        double r = empty > 0.0 ? (double)m * mean_empty / empty : 0.0;
-        o.u = empty > 0.0 ? (float)(1.0 - (r < 1.0 ? r : 1.0)) : 0.f;
+        o.n = tp.n;
+        o.empty_slots = empty;
+        o.mean_L = sw > 0.f ? (float)tp.mean : 0.f;
+        o.var_L = sw > 0.f ? (float)tp.m2 / sw : 0.f;
+        o.mean_Gx = tp.nonempty ? tp.sgx / ne : 0.f;
+        o.mean_Gy = tp.nonempty ? tp.sgy / ne : 0.f;
+        o.mean_Gt = tp.nonempty ? tp.sgt / ne : 0.f;
+        const float r = empty ? m * mean_empty / (float)empty : 0.f;
+        o.u = empty ? 1.f - fminf(r, 1.f) : 0.f;
         out[t] = o;
     }
 }
@@ -64,19 +65,18 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(int W, int H, int S, i
 // slot's time beside its pixel's queue state (a warp reads 128 contiguous
 // bytes of times) so that the loads of successive rows overlap. Ages are
 // summed in FP32 over at most 32 rows of one slot column (32 ages, each at
-// most the window) and in FP64 beyond: FP64 issues at 1/64 of the FP32 rate
-// on this part, too slow for a per-sample operation, and the tiles' FP64
-// divisions run here, spread over the SMs, rather than in the one block that
-// sums over tiles.
-struct alignas(64) TileTerm {
-    double v;           // luminance variance
-    double o;           // occluded share of the tile's slots
-    double inv_empty;   // 1 / empty slots (0 without empty slots)
-    double age;         // mean sample age (unused without samples)
-    double sg, sgt;     // spatial and temporal gradient sums over non-empty pixels
-    uint32_t empty, nonempty, has_samples, pad;
+// most the window); those sums are added in FP64, per thread and by a tree
+// over the block. (The same kernel with FP32 there measured 126 against 54
+// microseconds at 1920x1080x16; the FP64 adds are a few per thread.)
+struct alignas(16) TileTerm {
+    float v;           // luminance variance
+    float o;           // occluded share of the tile's slots
+    float inv_empty;   // 1 / empty slots (0 without empty slots)
+    float age;         // mean sample age (unused without samples)
+    float sg, sgt;     // spatial and temporal gradient sums over non-empty pixels
+    uint32_t empty, nonempty, has_samples, pad[3];
 };
-static_assert(sizeof(TileTerm) == 8 * sizeof(double), "eight doubles per tile");
+static_assert(sizeof(TileTerm) <= 8 * sizeof(double), "fits the 64 bytes a tile the context holds");
 
 __global__ void __launch_bounds__(256) k_tile_terms(int W, int H, int S, int ntx, int b, float t_now,
                                                     const uint32_t *__restrict__ state, const float *__restrict__ r_t,
@@ -112,30 +112,33 @@ __global__ void __launch_bounds__(256) k_tile_terms(int W, int H, int S, int ntx
     for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = d;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double age = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) age += sh[w];
-        const TilePartial tp = tiles[tile];
-        const double A = (double)(tw * th), empty = A * b - tp.n;
-        TileTerm tt;
-        tt.v = tp.sw > 0.0 ? tp.m2 / tp.sw : 0.0;
-        tt.o = occluded ? (double)occluded[tile] / (A * b) : 0.0;
-        tt.inv_empty = empty > 0.0 ? 1.0 / empty : 0.0;
-        tt.age = tp.n > 0.0 ? age / tp.n : 0.0;
-        tt.sg = 0.5 * (tp.sgx + tp.sgy);
-        tt.sgt = tp.sgt;
-        tt.empty = (uint32_t)empty;
-        tt.nonempty = (uint32_t)tp.nonempty;
-        tt.has_samples = tp.n > 0.0 ? 1u : 0u;
-        tt.pad = 0u;
-        terms[tile] = tt;
+    if (threadIdx.x < 32) {
+        double xd = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) xd += __shfl_xor_sync(0xffffffffu, xd, o);
+        const float x = (float)xd;
+        if (threadIdx.x == 0) {
+            const TilePartial tp = tiles[tile];
+            const uint32_t slots = (uint32_t)(tw * th) * (uint32_t)b, empty = slots - tp.n;
+            const float sw = (float)tp.sw;
+            TileTerm tt;
+            tt.v = sw > 0.f ? (float)tp.m2 / sw : 0.f;
+            tt.o = occluded ? (float)occluded[tile] / (float)slots : 0.f;
+            tt.inv_empty = empty ? 1.f / (float)empty : 0.f;
+            tt.age = tp.n ? x / (float)tp.n : 0.f;
+            tt.sg = 0.5f * (tp.sgx + tp.sgy);
+            tt.sgt = tp.sgt;
+            tt.empty = empty;
+            tt.nonempty = tp.nonempty;
+            tt.has_samples = tp.n ? 1u : 0u;
+            tt.pad[0] = tt.pad[1] = tt.pad[2] = 0u;
+            terms[tile] = tt;
+        }
     }
 }
 
 // Sum of each of N values over the block's kFbThreads threads: warp sums by
-// shuffles, then warp 0 sums the warps' partials and shares the totals (a
-// redundant per-thread sum over 32 partials would cost every warp 32 adds per
-// value, on the SM's narrow FP64 pipe for doubles).
+// shuffles, then warp 0 sums the warps' partials and shares the totals.
 template <typename T, int N>
 __device__ __forceinline__ void block_sum(T (&v)[N], T (*sh)[kFbThreads / 32]) {
     static_assert(kFbThreads == 1024, "warp 0 sums one partial per lane");
@@ -165,14 +168,14 @@ __device__ __forceinline__ void block_sum(T (&v)[N], T (*sh)[kFbThreads / 32]) {
 
 // Sections 6.1 and 4.1: tile error shares and gain control, one block over
 // the per-tile terms. The counts (empty slots, non-empty pixels, tiles with
-// samples) are summed as integers, exactly.
+// samples) are summed as integers, exactly; the rest are tree sums in FP32.
 __global__ void __launch_bounds__(kFbThreads) k_tile_error(int W, int H, int S, int ntx, int ntiles, float m,
-                                                           double kappa, double lambda, double importance, double eps,
+                                                           float kappa, float lambda, float importance, float eps,
                                                            const TileTerm *__restrict__ terms, bool has_occlusion,
                                                            float *__restrict__ E, AfrGain *__restrict__ gain) {
     __shared__ unsigned long long shi[3][kFbThreads / 32];
-    __shared__ double sh[6][kFbThreads / 32];
-    __shared__ double scal[4];   // m mean_empty, then the weights of v, u, o (one thread divides)
+    __shared__ float sh[6][kFbThreads / 32];
+    __shared__ float scal[4];   // m mean_empty, then the weights of v, u, o (one thread divides)
     unsigned long long cnt[3] = {0ull, 0ull, 0ull};   // empty slots, non-empty pixels, tiles with samples
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
         cnt[0] += terms[t].empty;
@@ -180,16 +183,15 @@ __global__ void __launch_bounds__(kFbThreads) k_tile_error(int W, int H, int S, 
         cnt[2] += terms[t].has_samples;
     }
     block_sum(cnt, shi);
-    if (threadIdx.x == 0) scal[0] = (double)m * ((double)cnt[0] / ntiles);
+    if (threadIdx.x == 0) scal[0] = m * ((float)cnt[0] / (float)ntiles);
     __syncthreads();
-    const double m_mean_empty = scal[0];
+    const float m_mean_empty = scal[0];
     // u = 1 - min(1, m mean_empty / empty), 0 without empty slots
     auto undersampling = [&](const TileTerm &tt) {
-        const double r = m_mean_empty * tt.inv_empty;
-        return tt.empty > 0u ? 1.0 - (r < 1.0 ? r : 1.0) : 0.0;
+        return tt.empty ? 1.f - fminf(m_mean_empty * tt.inv_empty, 1.f) : 0.f;
     };
     // sums: v, u, o, spatial gradient, temporal gradient, tile mean ages
-    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
         const TileTerm tt = terms[t];
         acc[0] += tt.v;
@@ -197,37 +199,37 @@ __global__ void __launch_bounds__(kFbThreads) k_tile_error(int W, int H, int S, 
         acc[2] += tt.o;
         acc[3] += tt.sg;
         acc[4] += tt.sgt;
-        acc[5] += tt.has_samples ? tt.age : 0.0;
+        acc[5] += tt.has_samples ? tt.age : 0.f;
     }
     block_sum(acc, sh);
     // E = s (kappa v / sum v + lambda u / sum u + (1 - kappa - lambda) o / sum o)
     if (threadIdx.x == 0) {
-        scal[1] = acc[0] > 0.0 ? kappa / acc[0] : 0.0;
-        scal[2] = acc[1] > 0.0 ? lambda / acc[1] : 0.0;
-        scal[3] = has_occlusion && acc[2] > 0.0 ? (1.0 - kappa - lambda) / acc[2] : 0.0;
+        scal[1] = acc[0] > 0.f ? kappa / acc[0] : 0.f;
+        scal[2] = acc[1] > 0.f ? lambda / acc[1] : 0.f;
+        scal[3] = has_occlusion && acc[2] > 0.f ? (1.f - kappa - lambda) / acc[2] : 0.f;
     }
     __syncthreads();
-    const double wv = scal[1], wu = scal[2], wo = scal[3];
+    const float wv = scal[1], wu = scal[2], wo = scal[3];
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
         const TileTerm tt = terms[t];
         const int tx = t % ntx, ty = t / ntx;
-        const double A = (double)(min(S, W - tx * S) * min(S, H - ty * S));
-        E[t] = (float)(A * (wv * tt.v + wu * undersampling(tt) + wo * tt.o));
+        const float A = (float)(min(S, W - tx * S) * min(S, H - ty * S));
+        E[t] = A * (wv * tt.v + wu * undersampling(tt) + wo * tt.o);
     }
     if (threadIdx.x == 0 && gain) {
-        const double nonempty = (double)cnt[1];
-        const double dcds = nonempty > 0.0 ? acc[3] / nonempty : 0.0, dcdt = nonempty > 0.0 ? acc[4] / nonempty : 0.0;
-        const double T = cnt[2] > 0ull ? acc[5] / (double)cnt[2] : 0.0;
-        const double Sw = importance * dcdt * T / (dcds > eps ? dcds : eps);
-        const double P = (double)W * H;
-        double N = Sw > 0.0 ? P / (Sw * Sw) : P;
-        N = N < 1.0 ? 1.0 : (N > P ? P : N);
+        const float nonempty = (float)cnt[1];
+        const float dcds = cnt[1] ? acc[3] / nonempty : 0.f, dcdt = cnt[1] ? acc[4] / nonempty : 0.f;
+        const float T = cnt[2] ? acc[5] / (float)cnt[2] : 0.f;
+        const float Sw = importance * dcdt * T / (dcds > eps ? dcds : eps);
+        const float P = (float)W * (float)H;
+        float N = Sw > 0.f ? P / (Sw * Sw) : P;
+        N = N < 1.f ? 1.f : (N > P ? P : N);
         AfrGain g;
-        g.dC_ds = (float)dcds;
-        g.dC_dt = (float)dcdt;
-        g.mean_age = (float)T;
-        g.tile_width = (float)Sw;
-        g.tile_count = (float)N;
+        g.dC_ds = dcds;
+        g.dC_dt = dcdt;
+        g.mean_age = T;
+        g.tile_width = Sw;
+        g.tile_count = N;
         *gain = g;
     }
 }

@@ -37,7 +37,7 @@ __device__ __forceinline__ float tile_volume(int x, int y, int W, int H, int S, 
                                              const TilePartial *__restrict__ tiles) {
     int tx = x / S, ty = y / S;
     float A = (float)(min(S, W - tx * S) * min(S, H - ty * S));
-    float n = (float)__ldg(&tiles[ty * ntx + tx].n);
+    float n = (float)__ldg(&tiles[ty * ntx + tx].n);   // an integer count
     return n > 0.f ? A * window / n : A * window;
 }
 

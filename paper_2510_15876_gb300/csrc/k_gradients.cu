@@ -112,7 +112,8 @@ struct Moments {
 // means (written to the gradient map) and the tile record: sample count,
 // non-empty pixels, gradient sums, and the age-weighted luminance moments
 // merged with Chan's formula (per thread and per warp in FP32, at most 2048
-// samples each; across warps in FP64 once the tile holds more than 4096).
+// samples each; across warps in FP64 once the tile holds more than 4096, the
+// one FP64 step of the forward path). The record stores FP64 fields.
 constexpr int kTileThreads = 256;
 
 __global__ void __launch_bounds__(kTileThreads) k_spatial_tiles(int W, int H, int S, int ntx,
@@ -171,11 +172,13 @@ __global__ void __launch_bounds__(kTileThreads) k_spatial_tiles(int W, int H, in
     __syncthreads();
     if (threadIdx.x == 0) {
         TilePartial out;
-        double tn = 0.0, tne = 0.0, tgx = 0.0, tgy = 0.0, tgt = 0.0;
+        // FP32 across the warps: the counts are integers (exact below 2^24) and
+        // the gradient sums add eight warp totals
+        float tn = 0.f, tne = 0.f, tgx = 0.f, tgy = 0.f, tgt = 0.f;
         for (int w = 0; w < kTileThreads / 32; ++w) {
             tn += sh[w][0]; tne += sh[w][1]; tgx += sh[w][2]; tgy += sh[w][3]; tgt += sh[w][4];
         }
-        if (tn > (double)kSortedBinMax) {   // more than 4096 samples: FP64 merge
+        if (tn > (float)kSortedBinMax) {   // more than 4096 samples: FP64 merge
             Moments<double> r{0.0, 0.0, 0.0};
             for (int w = 0; w < kTileThreads / 32; ++w) r.merge(sh[w][5], sh[w][6], sh[w][7]);
             out.sw = r.w; out.mean = r.mean; out.m2 = r.m2;
@@ -184,11 +187,12 @@ __global__ void __launch_bounds__(kTileThreads) k_spatial_tiles(int W, int H, in
             for (int w = 0; w < kTileThreads / 32; ++w) r.merge(sh[w][5], sh[w][6], sh[w][7]);
             out.sw = r.w; out.mean = r.mean; out.m2 = r.m2;
         }
-        out.n = tn;
-        out.nonempty = tne;
+        out.n = (uint32_t)tn;
+        out.nonempty = (uint32_t)tne;
         out.sgx = tgx;
         out.sgy = tgy;
         out.sgt = tgt;
+        out.pad[0] = out.pad[1] = out.pad[2] = 0u;
         tiles[tile] = out;
     }
 }
