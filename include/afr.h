@@ -381,15 +381,18 @@ AFR_API AfrStatus afr_batch_reconstruct(AfrBatch *batch, float t_now, const AfrP
  *   off_dev      width*height+1 uint32: record offset of each pixel's bin
  *   rec_dev      n x float4 (x', y', a^2, bin column as int32 bits)
  *   col_dev      n colours in color_type (16 or 8 bytes each)
- *   seq_dev      n uint32: batch index of each record; within a bin records
- *                are ordered by batch index
+ *   seq_dev      n uint32: batch index of each record; within a bin of up to
+ *                4096 records, records are ordered by batch index; a larger
+ *                bin holds its records in an unspecified order (as
+ *                afr_reproject keeps such bins in arrival order)
  *   n_frame_dev  1 uint32: number of records written (may be NULL)
  * The only scratch is one fixed device array of about 4 MB built into the
  * library, held by every GPU that loads it until the process exits; it
  * bounds width*height to 1,048,576 pixels, and n is bounded by 2^26. Larger
  * sizes return AFR_ERR_INVALID_ARG, like null or misaligned pointers. The
  * array's device address is looked up on the first call made with each
- * device current (make that call before any stream capture). All calls
+ * device current (make that call before any stream capture) and cached, so
+ * calls made after a cudaDeviceReset are undefined. All calls
  * share the array, so calls that overlap on the GPU race and must be
  * serialised by the caller. Asynchronous on the stream. */
 AFR_API AfrStatus afr_reproject_batch_static(const AfrSampleBatch *batch, uint32_t n, int32_t width,

@@ -33,10 +33,9 @@ cudaError_t dalloc(T **p, size_t n) {
 }
 
 void free_all(AfrContext *c) {
-    void *ptrs[] = {c->r_xy, c->r_mo, c->r_t, c->r_depth, c->r_seq, c->r_col, c->r_state, c->bin_of,
-                    c->pack,
-                    c->pcnt, c->poff, c->lbar, c->grad, c->pstat, c->sigma, c->tile_terms, c->fconst, c->cov_r[0], c->cov_r[1], c->cov_n, c->amin2, c->tiles, c->fcnt,
-                    c->foff, c->fpos, c->fcol, c->fseq, c->q_xy, c->q_mo, c->q_t, c->q_seq, c->q_col, c->q_total, c->q_world, c->r_world, c->scan_tmp, c->bgrad, c->bparam, c->dcount, c->derr};
+    void *ptrs[] = {c->r_xy, c->r_mo, c->r_t, c->r_depth, c->r_seq, c->r_col, c->r_state, c->bucket, c->fifo_flag, c->fifo_rank, c->fifo_scan,
+                    c->ccnt, c->coff, c->ccur, c->lbar, c->grad, c->pstat, c->sigma, c->tile_terms, c->fconst, c->cov_r[0], c->cov_r[1], c->cov_n, c->amin2, c->tiles, c->fcnt,
+                    c->foff, c->fpos, c->fcol, c->fseq, c->flist, c->q_xy, c->q_mo, c->q_t, c->q_seq, c->q_col, c->q_total, c->q_world, c->r_world, c->scan_tmp, c->bgrad, c->bparam, c->dcount, c->derr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -73,6 +72,26 @@ void widen_colors(int ct, const void *src, size_t i, float *dst3) {
 }  // namespace
 
 namespace afr {
+
+int device_sms() {
+    constexpr int kMaxDevices = 64;
+    static int cached[kMaxDevices] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return 1;
+    }
+    if (cached[dev] == 0) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+            cudaGetLastError();
+            return 1;
+        }
+        cached[dev] = sms;
+    }
+    return cached[dev];
+}
+
 namespace {
 __global__ void k_resident(const uint32_t *state, int P, unsigned long long *out) {
     unsigned long long acc = 0;
@@ -138,7 +157,7 @@ AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
     c->csize = c->ct == AFR_F32 ? 16 : 8;
     c->fifo_n = g.fifo_capacity;
     c->frame_cap = std::max(c->nslots, c->fifo_n);
-    c->scan_tmp_n = afr::scan_tmp_elems(c->P);
+    c->scan_tmp_n = afr::scan_tmp_elems(std::max<size_t>((size_t)c->P, (size_t)(((c->W + 15) / 16) * ((c->H + 7) / 8)) * 8));
     c->n_bblocks = afr::backward_blocks(c->W, c->H);
     cudaError_t e = cudaSuccess;
     size_t P = c->P, N = c->nslots;
@@ -151,8 +170,11 @@ AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
     AFR_ALLOC(c->r_seq, N);
     if (e == cudaSuccess) e = cudaMalloc(&c->r_col, N * c->csize);
     AFR_ALLOC(c->r_state, P);
-    AFR_ALLOC(c->pcnt, P);
-    AFR_ALLOC(c->poff, P + 1);
+    c->ncells = ((c->W + 15) / 16) * ((c->H + 7) / 8);
+    const size_t nkeys = (size_t)c->ncells * afr::ingest_sub_buckets();
+    AFR_ALLOC(c->ccnt, nkeys);
+    AFR_ALLOC(c->coff, nkeys + 1);
+    AFR_ALLOC(c->ccur, nkeys);
     AFR_ALLOC(c->lbar, P);
     AFR_ALLOC(c->grad, P);
     AFR_ALLOC(c->pstat, P);
@@ -178,9 +200,10 @@ AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
         AFR_ALLOC(c->q_total, 1);
         if (e == cudaSuccess) e = cudaMemset(c->q_total, 0, sizeof(uint32_t));
     }
-    AFR_ALLOC(c->fpos, 2 * c->frame_cap);
-    if (e == cudaSuccess) e = cudaMalloc(&c->fcol, 2 * c->frame_cap * c->csize);
-    AFR_ALLOC(c->fseq, 2 * c->frame_cap);
+    AFR_ALLOC(c->fpos, c->frame_cap);
+    if (e == cudaSuccess) e = cudaMalloc(&c->fcol, c->frame_cap * c->csize);
+    AFR_ALLOC(c->fseq, c->frame_cap);
+    AFR_ALLOC(c->flist, c->frame_cap);
     AFR_ALLOC(c->scan_tmp, c->scan_tmp_n);
     AFR_ALLOC(c->bgrad, 2 * P);
     AFR_ALLOC(c->bparam, (size_t)c->n_bblocks * 6);
@@ -230,12 +253,11 @@ AfrStatus afr_reset(AfrContext *c, afr_stream_t stream) {
 }
 
 static void free_batch(AfrContext *c) {
-    void *ptrs[] = {c->bin_of, c->pack, c->fifo_flag, c->fifo_rank, c->fifo_scan};
+    void *ptrs[] = {c->bucket, c->fifo_flag, c->fifo_rank, c->fifo_scan};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    c->bucket = nullptr;
     c->fifo_flag = c->fifo_rank = c->fifo_scan = nullptr;
-    c->bin_of = nullptr;
-    c->pack = nullptr;
     c->batch_cap = 0;
 }
 
@@ -245,8 +267,7 @@ AfrStatus afr_reserve(AfrContext *c, uint32_t n) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(c, e, "afr_reserve");
     free_batch(c);
-    e = dalloc(&c->bin_of, n);
-    if (e == cudaSuccess) e = cudaMalloc(&c->pack, (size_t)n * afr::packed_bytes(c->ct));
+    e = dalloc(&c->bucket, 4 * (size_t)n);
     if (c->fifo_n) {
         if (e == cudaSuccess) e = dalloc(&c->fifo_flag, n);
         if (e == cudaSuccess) e = dalloc(&c->fifo_rank, (size_t)n + 1);   // the scan also writes the total
@@ -531,8 +552,8 @@ AfrStatus afr_export_map(AfrContext *c, AfrMap which, float *map_host) {
     size_t P = c->P;
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(c, e, "afr_export_map");
-    if (which == AFR_MAP_LBAR) {
-        e = cudaMemcpy(map_host, c->lbar, P * 4, cudaMemcpyDeviceToHost);
+    if (which == AFR_MAP_LBAR) {   // the high part of the double-float mean
+        e = cudaMemcpy2D(map_host, 4, c->lbar, 8, 4, P, cudaMemcpyDeviceToHost);
     } else if (which >= AFR_MAP_GX && which <= AFR_MAP_GT) {
         e = cudaMemcpy2D(map_host, 4, reinterpret_cast<float *>(c->grad) + (which - AFR_MAP_GX), 16, 4, P,
                          cudaMemcpyDeviceToHost);
@@ -557,8 +578,9 @@ AfrStatus afr_import_map(AfrContext *c, AfrMap which, const float *map_host) {
     size_t P = c->P;
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(c, e, "afr_import_map");
-    if (which == AFR_MAP_LBAR) {
-        e = cudaMemcpy(c->lbar, map_host, P * 4, cudaMemcpyHostToDevice);
+    if (which == AFR_MAP_LBAR) {   // imported means have no low part
+        e = cudaMemset(c->lbar, 0, P * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMemcpy2D(c->lbar, 8, map_host, 4, 4, P, cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
             e = cudaMemcpy2D(reinterpret_cast<float *>(c->grad) + 3, 16, map_host, 4, 4, P, cudaMemcpyHostToDevice);
     } else if (which >= AFR_MAP_GX && which <= AFR_MAP_GT) {

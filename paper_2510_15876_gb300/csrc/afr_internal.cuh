@@ -95,14 +95,17 @@ struct AfrContext {
     uint32_t *fifo_flag = nullptr;  // [batch_cap] 1 for an accepted sample
     uint32_t *fifo_rank = nullptr;  // [batch_cap + 1] exclusive scan of fifo_flag, then the total
     uint32_t *fifo_scan = nullptr;  // scan block sums for batch_cap entries
-    uint2 *bin_of = nullptr;      // [batch_cap] (pixel, ticket within the pixel) of each sample (kInvalid: rejected)
-    void *pack = nullptr;         // [batch_cap] 64-byte sample records in pixel order
+    // ingest scratch: per-cell counts and offsets (cells of 16 x 8 pixels) and
+    // the batch's bucket planes in cell order (batch_cap records)
+    int ncells = 0;
+    uint32_t *ccnt = nullptr;     // [ncells * sub-buckets] bucket counts
+    uint32_t *coff = nullptr;     // [ncells * sub-buckets + 1] bucket offsets
+    uint32_t *ccur = nullptr;     // [ncells * sub-buckets] append cursors
+    uint4 *bucket = nullptr;      // [4 * batch_cap] 64-byte sample records in bucket order
     size_t batch_cap = 0;
-    uint32_t *pcnt = nullptr;     // [P]
-    uint32_t *poff = nullptr;     // [P+1]
 
     // maps
-    float *lbar = nullptr;        // [P]
+    float2 *lbar = nullptr;       // [P] weighted mean luminance as double-float (hi, lo)
     float4 *grad = nullptr;       // [P] (Gx, Gy, Gt, Lbar)
     float4 *pstat = nullptr;      // [P] (sum w, mean L, M2, Gt)
     float2 *sigma = nullptr;      // [P] (sigma_s, sigma_t)
@@ -119,9 +122,10 @@ struct AfrContext {
     // frame view
     uint32_t *fcnt = nullptr;     // [P]
     uint32_t *foff = nullptr;     // [P+1]
-    float4 *fpos = nullptr;       // [2*frame_cap] (x', y', a^2, bin column as int bits)
-    void *fcol = nullptr;         // [2*frame_cap]
-    uint32_t *fseq = nullptr;     // [2*frame_cap] sequence numbers
+    float4 *fpos = nullptr;       // [frame_cap] (x', y', a^2, bin column as int bits)
+    void *fcol = nullptr;         // [frame_cap]
+    uint32_t *fseq = nullptr;     // [frame_cap] sequence numbers
+    uint32_t *flist = nullptr;    // [frame_cap] each bin's source slots, unordered (reprojection scratch)
     size_t frame_cap = 0;
 
     // scan scratch
@@ -196,6 +200,64 @@ __device__ __forceinline__ float luminance(float3 c) {
     return fmaf(kLumB, c.z, fmaf(kLumG, c.y, kLumR * c.x));
 }
 
+// ---- double-float arithmetic ------------------------------------------------
+// A value held as the unevaluated sum h + l of two floats (|l| <= ulp(h)/2),
+// about 48 significant bits from FP32 operations only. Built on the error-free
+// transformations TwoSum (Knuth) and TwoProduct with a fused multiply-add
+// (Ogita, Rump and Oishi, "Accurate sum and dot product", 2005). The spatial
+// and temporal gradients subtract luminances that agree in most of their
+// bits; holding the luminances and their weighted means in this form keeps
+// those differences accurate to FP32 rounding of the difference itself.
+struct dfloat {
+    float h, l;
+};
+
+__device__ __forceinline__ dfloat two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ dfloat fast_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfloat two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
+    const dfloat s = two_sum(a.h, b.h);
+    const dfloat t = two_sum(a.l, b.l);
+    dfloat r = fast_two_sum(s.h, __fadd_rn(s.l, t.h));
+    return fast_two_sum(r.h, __fadd_rn(r.l, t.l));
+}
+__device__ __forceinline__ dfloat df_mul(dfloat a, float b) {
+    dfloat p = two_prod(a.h, b);
+    return fast_two_sum(p.h, __fmaf_rn(a.l, b, p.l));
+}
+__device__ __forceinline__ dfloat df_div(dfloat a, dfloat b) {
+    const float q1 = __fdiv_rn(a.h, b.h);
+    const dfloat r = df_add(a, df_mul({-b.h, -b.l}, q1));
+    const float q2 = __fdiv_rn(r.h, b.h);
+    return fast_two_sum(q1, q2);
+}
+// a - b rounded once to float
+__device__ __forceinline__ float df_diff(dfloat a, dfloat b) {
+    return __fadd_rn(__fsub_rn(a.h, b.h), __fsub_rn(a.l, b.l));
+}
+
+// Rec. 709 luminance in double-float: each weight is split into the float
+// nearest to it and the float nearest to the remainder.
+__device__ __forceinline__ dfloat luminance_df(float3 c) {
+    constexpr double kR = 0.2126, kG = 0.7152, kB = 0.0722;
+    constexpr float rh = (float)kR, gh = (float)kG, bh = (float)kB;
+    constexpr float rl = (float)(kR - (double)rh), gl = (float)(kG - (double)gh), bl = (float)(kB - (double)bh);
+    dfloat s = df_mul({rh, rl}, c.x);
+    s = df_add(s, df_mul({gh, gl}, c.y));
+    return df_add(s, df_mul({bh, bl}, c.z));
+}
+
 // 2^x with the hardware approximation (relative error below 2^-22).
 __device__ __forceinline__ float ex2(float x) {
     float y;
@@ -241,7 +303,12 @@ __device__ __forceinline__ void agg_count(unsigned long long *ctr, bool flag) {
     if ((threadIdx.x & 31) == __ffs(mask) - 1 && bits) atomicAdd(ctr, (unsigned long long)__popc(bits));
 }
 
-inline int grid_for(size_t n, int block, int cap = 152 * 32) {
+// Multiprocessor count of the current device (read once per device).
+int device_sms();
+
+// Blocks for n items of a grid-stride kernel: at most 32 blocks per SM.
+inline int grid_for(size_t n, int block, int cap = 0) {
+    if (cap <= 0) cap = 32 * device_sms();
     size_t g = (n + block - 1) / block;
     if (g < 1) g = 1;
     if (g > (size_t)cap) g = cap;
@@ -270,9 +337,9 @@ cudaError_t launch_set_frame_colors(AfrContext *c, const float *rgb, cudaStream_
 int backward_blocks(int W, int H);
 cudaError_t launch_batch(int ct, const BatchCtx *cs, int nctx, uint32_t nchunks, uint32_t total, uint32_t *queue,
                          int grid, cudaStream_t s);
-size_t packed_bytes(int ct);
 constexpr int kBatchSigmaChunk = 2048;   // pixels per width chunk of a batched launch
 constexpr int kBatchDirectPixels = 131072;   // larger contexts of a batch get their own launches
 cudaError_t launch_resident_count(AfrContext *c, cudaStream_t s);
+int ingest_sub_buckets();
 
 }  // namespace afr

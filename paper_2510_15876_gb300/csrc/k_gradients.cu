@@ -23,10 +23,21 @@ __device__ __forceinline__ float group_sum(float v) {
     return v;
 }
 
+// Luminance differences carry the gradients: the spatial gradient is a
+// difference of neighbouring pixel means and the temporal one a difference
+// of consecutive luminances, both far smaller than the luminances. So each
+// pixel takes the luminance of its newest sample, in double-float, as its
+// reference L_r, and every sample its deviation d = L - L_r in FP32 from the
+// colour differences (exact when the colours are within a factor 2, else
+// rounded once), whose error scales with the pixel's spread of luminance,
+// not its level. The mean is L_r + sum(w d) / sum(w), kept as (hi, lo); the
+// temporal gradient takes each consecutive pair's difference from its colour
+// differences; the age weights, the time steps and the variance moments are
+// FP32.
 template <int CT, int G>
 __global__ void __launch_bounds__(256) k_pixel(int P, int b, float t_now, const uint32_t *__restrict__ state,
                                                const float *__restrict__ r_t, const uint32_t *__restrict__ r_seq,
-                                               const void *__restrict__ r_col, float *__restrict__ lbar,
+                                               const void *__restrict__ r_col, float2 *__restrict__ lbar,
                                                float4 *__restrict__ pstat) {
     using CS = ColorStore<CT>;
     const int k = threadIdx.x & (G - 1);
@@ -38,7 +49,8 @@ __global__ void __launch_bounds__(256) k_pixel(int P, int b, float t_now, const 
         uint32_t st = pix ? __ldg(state + p) : 0u;
         int n = (int)(st & 0xFFFFu), h = (int)(st >> 16);
         bool valid = k < n;
-        float T = -INFINITY, L = 0.f, w = 0.f;
+        float T = -INFINITY, w = 0.f;
+        float3 c = make_float3(0.f, 0.f, 0.f);
         uint32_t Q = 0;
         if (valid) {
             int s = h - 1 - k;
@@ -46,14 +58,19 @@ __global__ void __launch_bounds__(256) k_pixel(int P, int b, float t_now, const 
             size_t i = (size_t)p * b + s;
             T = __ldg(r_t + i);
             Q = __ldg(r_seq + i);
-            L = luminance(CS::load(r_col, i));
+            c = CS::load(r_col, i);
             w = expf(-kAgeDecay * fmaxf(t_now - T, 0.f));
         }
-        float sw = group_sum<G>(w);
-        float swl = group_sum<G>(w * L);
-        float mean = n > 0 ? swl / sw : 0.f;
-        float d = valid ? L - mean : 0.f;
-        float m2 = group_sum<G>(w * d * d);
+        // reference: the newest sample (lane 0 of the group)
+        const float3 cr = make_float3(__shfl_sync(0xffffffffu, c.x, 0, G), __shfl_sync(0xffffffffu, c.y, 0, G),
+                                      __shfl_sync(0xffffffffu, c.z, 0, G));
+        float D = 0.f;   // L - L_r
+        if (valid) D = fmaf(kLumB, __fsub_rn(c.z, cr.z), fmaf(kLumG, __fsub_rn(c.y, cr.y), kLumR * __fsub_rn(c.x, cr.x)));
+        const float sw = group_sum<G>(w);
+        const float swd = group_sum<G>(w * D);
+        const float delta = n > 0 ? swd / sw : 0.f;   // mean - L_r
+        const float dd = valid ? D - delta : 0.f;
+        const float m2 = group_sum<G>(w * dd * dd);
         // newest first by time, equal times newest first by sequence number;
         // queues filled in time order are already in that order
         float Tn = __shfl_down_sync(0xffffffffu, T, 1, G);
@@ -67,28 +84,35 @@ __global__ void __launch_bounds__(256) k_pixel(int P, int b, float t_now, const 
                 for (int j = kk >> 1; j > 0; j >>= 1) {
                     float To = __shfl_xor_sync(0xffffffffu, T, j, G);
                     uint32_t Qo = __shfl_xor_sync(0xffffffffu, Q, j, G);
-                    float Lo = __shfl_xor_sync(0xffffffffu, L, j, G);
+                    float cxo = __shfl_xor_sync(0xffffffffu, c.x, j, G);
+                    float cyo = __shfl_xor_sync(0xffffffffu, c.y, j, G);
+                    float czo = __shfl_xor_sync(0xffffffffu, c.z, j, G);
                     float wo = __shfl_xor_sync(0xffffffffu, w, j, G);
                     bool mine_first = (T > To) || (T == To && Q > Qo);   // descending order
                     bool lower = (k & j) == 0, desc = (k & kk) == 0;
                     bool keep = (lower == desc) ? mine_first : !mine_first;
-                    if (!keep) { T = To; Q = Qo; L = Lo; w = wo; }
+                    if (!keep) { T = To; Q = Qo; c = make_float3(cxo, cyo, czo); w = wo; }
                 }
             }
         }
-        float Ln = __shfl_down_sync(0xffffffffu, L, 1, G);
+        // consecutive luminance differences from the colour differences
+        const float3 cn = make_float3(__shfl_down_sync(0xffffffffu, c.x, 1, G), __shfl_down_sync(0xffffffffu, c.y, 1, G),
+                                      __shfl_down_sync(0xffffffffu, c.z, 1, G));
         Tn = __shfl_down_sync(0xffffffffu, T, 1, G);
         bool pair = k + 1 < n;
-        float num = group_sum<G>(pair ? w * fabsf(L - Ln) : 0.f);
+        const float dL = fmaf(kLumB, __fsub_rn(c.z, cn.z), fmaf(kLumG, __fsub_rn(c.y, cn.y), kLumR * __fsub_rn(c.x, cn.x)));
+        float num = group_sum<G>(pair ? w * fabsf(dL) : 0.f);
         float den = group_sum<G>(pair ? w * (T - Tn) : 0.f);
         if (k == 0 && pix) {
             if (n == 0) {
-                lbar[p] = __int_as_float(0x7fc00000);
+                lbar[p] = make_float2(__int_as_float(0x7fc00000), 0.f);
                 pstat[p] = make_float4(0.f, 0.f, 0.f, 0.f);
             } else {
+                const dfloat Lr = luminance_df(cr);
+                const dfloat mean = df_add(Lr, {delta, 0.f});
                 float gt = (n >= 2 && den > 0.f) ? num / den : 0.f;
-                lbar[p] = mean;
-                pstat[p] = make_float4(sw, mean, m2, gt);
+                lbar[p] = make_float2(mean.h, mean.l);
+                pstat[p] = make_float4(sw, mean.h, m2, gt);
             }
         }
     }
@@ -117,7 +141,7 @@ struct Moments {
 constexpr int kTileThreads = 256;
 
 __global__ void __launch_bounds__(kTileThreads) k_spatial_tiles(int W, int H, int S, int ntx,
-                                                                const float *__restrict__ lbar,
+                                                                const float2 *__restrict__ lbar,
                                                                 const float4 *__restrict__ pstat,
                                                                 const uint32_t *__restrict__ state,
                                                                 float4 *__restrict__ grad,
@@ -130,18 +154,22 @@ __global__ void __launch_bounds__(kTileThreads) k_spatial_tiles(int W, int H, in
     for (int k = threadIdx.x; k < A; k += blockDim.x) {
         const int x = x0 + k % tw, y = y0 + k / tw;
         const int p = y * W + x;
-        const float l = __ldg(lbar + p);
+        const float2 lp = __ldg(lbar + p);
+        const float l = lp.x;
         const float4 ps = __ldg(pstat + p);
         if (isnan(l)) {
             grad[p] = make_float4(0.f, 0.f, 0.f, l);
             continue;
         }
-        float sx = 0.f, sy = 0.f, v;
+        // one-sided differences of the double-float means, rounded once
+        float sx = 0.f, sy = 0.f;
         int mx = 0, my = 0;
-        if (x > 0 && !isnan(v = __ldg(lbar + p - 1))) { sx += fabsf(l - v); ++mx; }
-        if (x + 1 < W && !isnan(v = __ldg(lbar + p + 1))) { sx += fabsf(l - v); ++mx; }
-        if (y > 0 && !isnan(v = __ldg(lbar + p - W))) { sy += fabsf(l - v); ++my; }
-        if (y + 1 < H && !isnan(v = __ldg(lbar + p + W))) { sy += fabsf(l - v); ++my; }
+        const dfloat lm = {lp.x, lp.y};
+        float2 v;
+        if (x > 0 && !isnan((v = __ldg(lbar + p - 1)).x)) { sx += fabsf(df_diff(lm, {v.x, v.y})); ++mx; }
+        if (x + 1 < W && !isnan((v = __ldg(lbar + p + 1)).x)) { sx += fabsf(df_diff(lm, {v.x, v.y})); ++mx; }
+        if (y > 0 && !isnan((v = __ldg(lbar + p - W)).x)) { sy += fabsf(df_diff(lm, {v.x, v.y})); ++my; }
+        if (y + 1 < H && !isnan((v = __ldg(lbar + p + W)).x)) { sy += fabsf(df_diff(lm, {v.x, v.y})); ++my; }
         const float gx = mx ? sx / mx : 0.f, gy = my ? sy / my : 0.f;
         grad[p] = make_float4(gx, gy, ps.w, l);
         n += (float)(__ldg(state + p) & 0xFFFFu);
@@ -199,7 +227,7 @@ __global__ void __launch_bounds__(kTileThreads) k_spatial_tiles(int W, int H, in
 
 template <int CT>
 cudaError_t launch_pixel(AfrContext *c, float t_now, cudaStream_t s) {
-    int g = grid_for((size_t)c->P * 32, 256, 152 * 16);
+    int g = grid_for((size_t)c->P * 32, 256, 16 * device_sms());
     if (c->b <= 4)
         k_pixel<CT, 4><<<g, 256, 0, s>>>(c->P, c->b, t_now, c->r_state, c->r_t, c->r_seq, c->r_col, c->lbar, c->pstat);
     else if (c->b <= 8)

@@ -1,151 +1,180 @@
-// k_ingest.cu -- section 4 deep buffer: counting-sort a batch of samples by
-// pixel and push each pixel's share into its queue of depth b.
+// k_ingest.cu -- section 4 deep buffer: push a batch of samples into the
+// per-pixel queues of depth b (each keeps its b newest samples by insertion
+// order).
 //
-//  1. hist:   validate each sample, record its pixel and its ticket (its rank
-//             among the pixel's samples in atomic order).
-//  2. scan:   pixel offsets of the counting sort.
-//  3. place:  write each sample, repacked into one 64-byte record that also
-//             carries its batch index, at offset + ticket. A warp stages its
-//             32 records in shared memory and stores them back four lanes per
-//             record, so every record is one whole 64-byte block (no partial
-//             sectors for the memory system to merge).
-//  4. commit: one warp per pixel reads the pixel's records (contiguous),
-//             ranks them by batch index (= insertion order): up to 32 records
-//             by counting smaller indices across the warp, more by a chunked
-//             bitonic top-32; keeps the min(b, m) newest and writes them into
-//             the circular queue at (head + rank) mod b, the slots sequential
-//             pushes would use.
+// The batch arrives in insertion order with its samples spread over the whole
+// image, and the queues are planes in pixel order, so ingest is a sort. It
+// runs through cells of 16 x 8 pixels:
+//
+//  1. count:   per bucket, the samples whose position is valid (reads only
+//              the 16-byte position of each sample). A cell's records go to
+//              kSubBuckets buckets by batch index modulo kSubBuckets, laid out
+//              one after another, so that the cell's bucket is still one
+//              contiguous range while each counter takes one eighth of the
+//              cell's atomics.
+//  2. scan:    bucket offsets.
+//  3. scatter: each sample appends its 64-byte record (position, colour,
+//              motion, batch index, hit point) to its bucket. A warp stages its
+//              32 records in shared memory and stores each with four lanes, so
+//              every store is two whole sectors; a thread takes the tickets of
+//              several samples before using any, to keep atomics in flight. A
+//              sample whose colour or motion is not finite leaves a dead
+//              record (batch index kInvalid).
+//  4. commit:  one CTA per cell reads its bucket once, sorts the records by
+//              pixel in shared memory, ranks each pixel's records by batch
+//              index (insertion order) and writes the newest min(b, m) to the
+//              queue slots (head + rank) mod b that sequential pushes would
+//              use, so a warp's stores cover consecutive slots. A cell with
+//              more records than one round of shared memory is committed in
+//              rounds over groups of its pixels; a pixel that alone holds
+//              more is ranked by a warp streaming the bucket and keeping the
+//              newest 32 in registers.
 #include "afr_internal.cuh"
 
 namespace afr {
 namespace {
 
-// 64-byte staging record: a = (x, y, t, depth); b = colour and motion;
-// c.y = batch index. F32: b = (r, g, b, m_x), c.x = m_y. 16-bit colours:
-// b = (r | g << 16, b, m_x, m_y).
-struct alignas(64) Rec64 {
-    uint4 a, b, c, d;
+constexpr int kCellW = 16, kCellH = 8, kCellPix = kCellW * kCellH;
+constexpr int kSubBuckets = 8;
+constexpr int kCommitCap = 3072;      // records of one round in shared memory
+constexpr int kCommitThreads = 512;
+constexpr int kCommitWarps = kCommitThreads / 32;
+
+// Bucket records, 64 bytes each as four uint4:
+//   q0 = (x, y, t, depth)
+//   q1 = (batch index, m_y for FP32 colours, hit point X, Y)
+//   q2 = FP32: (r, g, b, m_x); 16-bit: (r | g << 16, b, m_x, m_y)
+//   q3 = (hit point Z, 0, 0, 0)
+// The first sector (q0, q1) is all the commit's sort reads.
+struct Bucket {
+    uint4 *r;    // [4 * batch_cap]
+    bool world;  // records carry hit points
 };
 
-template <int CT> struct RecCodec;
-template <> struct RecCodec<AFR_F32> {
-    using T = float4;
-    static __device__ __forceinline__ void pack(Rec64 &r, float4 p, T col, float2 m, uint32_t i) {
-        r.a = make_uint4(__float_as_uint(p.x), __float_as_uint(p.y), __float_as_uint(p.z), __float_as_uint(p.w));
-        r.b = make_uint4(__float_as_uint(col.x), __float_as_uint(col.y), __float_as_uint(col.z),
-                         __float_as_uint(m.x));
-        r.c = make_uint4(__float_as_uint(m.y), i, 0u, 0u);
-        r.d = make_uint4(0u, 0u, 0u, 0u);
-    }
-    static __device__ __forceinline__ T color(uint4 b, uint4) {
-        return make_float4(__uint_as_float(b.x), __uint_as_float(b.y), __uint_as_float(b.z), 0.f);
-    }
-    static __device__ __forceinline__ float2 motion(uint4 b, uint4 c) {
-        return make_float2(__uint_as_float(b.w), __uint_as_float(c.x));
-    }
+// Destination planes of the queues (slot p * b + s).
+struct Queues {
+    float2 *xy, *mo;
+    float *t, *depth;
+    uint32_t *seq;
+    void *col;
+    uint32_t *state;   // count | head << 16
+    float4 *world;
 };
-struct RecCodec16 {
-    using T = ushort4;
-    static __device__ __forceinline__ void pack(Rec64 &r, float4 p, T col, float2 m, uint32_t i) {
-        r.a = make_uint4(__float_as_uint(p.x), __float_as_uint(p.y), __float_as_uint(p.z), __float_as_uint(p.w));
-        r.b = make_uint4((uint32_t)col.x | ((uint32_t)col.y << 16), (uint32_t)col.z, __float_as_uint(m.x),
-                         __float_as_uint(m.y));
-        r.c = make_uint4(0u, i, 0u, 0u);
-        r.d = make_uint4(0u, 0u, 0u, 0u);
-    }
-    static __device__ __forceinline__ T color(uint4 b, uint4) {
-        return make_ushort4((unsigned short)(b.x & 0xFFFFu), (unsigned short)(b.x >> 16), (unsigned short)b.y, 0);
-    }
-    static __device__ __forceinline__ float2 motion(uint4 b, uint4) {
-        return make_float2(__uint_as_float(b.z), __uint_as_float(b.w));
-    }
-};
-template <> struct RecCodec<AFR_F16> : RecCodec16 {};
-template <> struct RecCodec<AFR_BF16> : RecCodec16 {};
 
-template <int CT>
-__global__ void __launch_bounds__(256) k_hist(const float4 *__restrict__ pos, const void *__restrict__ col,
-                                              const float2 *__restrict__ mo, uint32_t n, int W, int H,
-                                              uint2 *__restrict__ bin_of, uint32_t *__restrict__ pcnt,
-                                              unsigned long long *__restrict__ dcount) {
-    using CS = ColorStore<CT>;
+__device__ __forceinline__ bool position_ok(float4 p, int W, int H) {
+    return isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && p.x >= 0.f && p.y >= 0.f && p.x < (float)W &&
+           p.y < (float)H;
+}
+
+__device__ __forceinline__ uint32_t cell_of(float x, float y, int ncx) {
+    const int qx = (int)floorf(x), qy = (int)floorf(y);
+    return (uint32_t)((qy / kCellH) * ncx + qx / kCellW);
+}
+
+__global__ void __launch_bounds__(256) k_cell_count(const float4 *__restrict__ pos, uint32_t n, int W, int H, int ncx,
+                                                    uint32_t *__restrict__ ccnt) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        float4 p = __ldg(pos + i);
-        typename CS::T cr = CS::raw(col, i);
-        float3 c = CS::widen(cr);
-        float2 m = __ldg(mo + i);
-        bool ok = isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(c.x) && isfinite(c.y) &&
-                  isfinite(c.z) && isfinite(m.x) && isfinite(m.y) && p.x >= 0.f && p.y >= 0.f &&
-                  p.x < (float)W && p.y < (float)H;
-        uint2 bt = make_uint2(kInvalid, 0u);
-        if (ok) {
-            bt.x = (uint32_t)(int)floorf(p.y) * (uint32_t)W + (uint32_t)(int)floorf(p.x);
-            bt.y = atomicAdd(pcnt + bt.x, 1u);   // a batch in time order rarely repeats a pixel within a warp
-        }
-        bin_of[i] = bt;
-        agg_count(dcount + CNT_REJECTED, !ok);
+        const float4 p = __ldg(pos + i);
+        if (position_ok(p, W, H)) atomicAdd(ccnt + cell_of(p.x, p.y, ncx) * kSubBuckets + (i & (kSubBuckets - 1)), 1u);
     }
 }
 
-// Each warp takes 32 consecutive samples: lanes build their records in
-// shared memory (80-byte stride: conflict-free 16-byte accesses), then lane
-// 4k + q stores part q of record 8r + k in round r.
-constexpr int kPlaceWarps = 8;
+template <int CT>
+__device__ __forceinline__ bool sample_ok(float4 p, typename ColorStore<CT>::T cr, float2 m, bool pok) {
+    const float3 c = ColorStore<CT>::widen(cr);
+    return pok && isfinite(c.x) && isfinite(c.y) && isfinite(c.z) && isfinite(m.x) && isfinite(m.y);
+}
+
+constexpr int kScatterWarps = 8;
+constexpr int kScatterUnroll = 4;   // samples (and ticket atomics) in flight per thread
 
 template <int CT>
-__global__ void __launch_bounds__(32 * kPlaceWarps) k_place(const float4 *__restrict__ pos,
-                                                            const void *__restrict__ col,
-                                                            const float2 *__restrict__ mo, uint32_t n,
-                                                            const uint2 *__restrict__ bin_of,
-                                                            const uint32_t *__restrict__ poff,
-                                                            const float4 *__restrict__ world,
-                                                            Rec64 *__restrict__ pk) {
+__global__ void __launch_bounds__(32 * kScatterWarps) k_cell_scatter(
+    const float4 *__restrict__ pos, const void *__restrict__ col, const float2 *__restrict__ mo,
+    const float4 *__restrict__ world, uint32_t n, int W, int H, int ncx, const uint32_t *__restrict__ coff,
+    uint32_t *__restrict__ ccur, Bucket bk, uint32_t *__restrict__ accept, unsigned long long *__restrict__ dcount) {
     using CS = ColorStore<CT>;
-    __shared__ uint4 stage[kPlaceWarps][32][5];
-    __shared__ uint32_t dest[kPlaceWarps][32];
+    __shared__ uint4 stage[kScatterWarps][32][5];   // 80-byte stride: conflict-free 16-byte accesses
+    __shared__ uint32_t dest[kScatterWarps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const uint32_t nwarps = gridDim.x * kPlaceWarps;
-    for (uint32_t base = (blockIdx.x * kPlaceWarps + w) * 32u; base < n; base += nwarps * 32u) {
-        const uint32_t i = base + lane;
-        uint32_t d = kInvalid;
-        if (i < n) {
-            const uint2 bt = bin_of[i];
-            if (bt.x != kInvalid) {
-                d = __ldg(poff + bt.x) + bt.y;
-                Rec64 r;
-                RecCodec<CT>::pack(r, __ldg(pos + i), CS::raw(col, i), __ldg(mo + i), i);
-                if (world) {   // hit point in the record's spare 16 bytes
-                    const float4 w = __ldg(world + i);
-                    r.d = make_uint4(__float_as_uint(w.x), __float_as_uint(w.y), __float_as_uint(w.z), 0u);
-                }
-                stage[w][lane][0] = r.a;
-                stage[w][lane][1] = r.b;
-                stage[w][lane][2] = r.c;
-                stage[w][lane][3] = r.d;
+    const uint32_t step = gridDim.x * kScatterWarps * 32u * kScatterUnroll;
+    for (uint32_t base = (blockIdx.x * kScatterWarps + w) * 32u * kScatterUnroll; base < n; base += step) {
+        float4 p[kScatterUnroll];
+        typename CS::T cr[kScatterUnroll];
+        float2 m[kScatterUnroll];
+#pragma unroll
+        for (int r = 0; r < kScatterUnroll; ++r) {
+            const uint32_t i = base + r * 32 + lane;
+            p[r] = make_float4(-1.f, -1.f, 0.f, 0.f);
+            if (i < n) {
+                p[r] = __ldg(pos + i);
+                cr[r] = CS::raw(col, i);
+                m[r] = __ldg(mo + i);
             }
         }
-        dest[w][lane] = d;
-        __syncwarp();
+        uint32_t d[kScatterUnroll];
+        bool ok[kScatterUnroll];
 #pragma unroll
-        for (int round = 0; round < 4; ++round) {
-            const int k = round * 8 + (lane >> 2), q = lane & 3;
-            const uint32_t dk = dest[w][k];
-            if (dk != kInvalid) reinterpret_cast<uint4 *>(pk + dk)[q] = stage[w][k][q];
+        for (int r = 0; r < kScatterUnroll; ++r) {
+            const uint32_t i = base + r * 32 + lane;
+            const bool in = i < n;
+            const bool pok = in && position_ok(p[r], W, H);
+            ok[r] = in && sample_ok<CT>(p[r], cr[r], m[r], pok);
+            agg_count(dcount + CNT_REJECTED, in && !ok[r]);
+            if (in && accept) accept[i] = ok[r] ? 1u : 0u;
+            d[r] = kInvalid;
+            if (pok) {
+                const uint32_t key = cell_of(p[r].x, p[r].y, ncx) * kSubBuckets + (i & (kSubBuckets - 1));
+                d[r] = __ldg(coff + key) + atomicAdd(ccur + key, 1u);
+            }
         }
-        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < kScatterUnroll; ++r) {
+            const uint32_t i = base + r * 32 + lane;
+            if (d[r] != kInvalid) {
+                float4 wp = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (bk.world && ok[r]) wp = __ldg(world + i);
+                uint4 q2;
+                uint32_t my = 0u;
+                if (CT == AFR_F32) {
+                    const float4 cf = *reinterpret_cast<const float4 *>(&cr[r]);
+                    q2 = make_uint4(__float_as_uint(cf.x), __float_as_uint(cf.y), __float_as_uint(cf.z),
+                                    __float_as_uint(m[r].x));
+                    my = __float_as_uint(m[r].y);
+                } else {
+                    const ushort4 h = *reinterpret_cast<const ushort4 *>(&cr[r]);
+                    q2 = make_uint4((uint32_t)h.x | ((uint32_t)h.y << 16), (uint32_t)h.z, __float_as_uint(m[r].x),
+                                    __float_as_uint(m[r].y));
+                }
+                stage[w][lane][0] = make_uint4(__float_as_uint(p[r].x), __float_as_uint(p[r].y),
+                                               __float_as_uint(p[r].z), __float_as_uint(p[r].w));
+                stage[w][lane][1] = make_uint4(ok[r] ? i : kInvalid, my, __float_as_uint(wp.x), __float_as_uint(wp.y));
+                stage[w][lane][2] = q2;
+                stage[w][lane][3] = make_uint4(__float_as_uint(wp.z), 0u, 0u, 0u);
+            }
+            dest[w][lane] = d[r];
+            __syncwarp();
+            // lane 4k + q stores part q of record 8 round + k
+#pragma unroll
+            for (int round = 0; round < 4; ++round) {
+                const int k = round * 8 + (lane >> 2), q = lane & 3;
+                const uint32_t dk = dest[w][k];
+                if (dk != kInvalid) bk.r[4 * (size_t)dk + q] = stage[w][k][q];
+            }
+            __syncwarp();
+        }
     }
 }
 
 // ascending bitonic sort of one 64-bit key per lane across a full warp
 __device__ __forceinline__ unsigned long long warp_sort_asc(unsigned long long v) {
-    int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
         for (int j = k >> 1; j > 0; j >>= 1) {
-            unsigned long long o = __shfl_xor_sync(0xffffffffu, v, j);
-            bool up = ((lane & k) == 0);
-            bool lower = ((lane & j) == 0);
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, j);
+            const bool up = ((lane & k) == 0), lower = ((lane & j) == 0);
             v = (lower == up) ? min(v, o) : max(v, o);
         }
     }
@@ -154,130 +183,372 @@ __device__ __forceinline__ unsigned long long warp_sort_asc(unsigned long long v
 
 // merge step of a bitonic sequence held across the warp into ascending order
 __device__ __forceinline__ unsigned long long warp_merge_asc(unsigned long long v) {
-    int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int j = 16; j > 0; j >>= 1) {
-        unsigned long long o = __shfl_xor_sync(0xffffffffu, v, j);
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, j);
         v = ((lane & j) == 0) ? min(v, o) : max(v, o);
     }
     return v;
 }
 
-// sort key of record e of a pixel's segment: (batch index + 1) << 32 | position
-__device__ __forceinline__ unsigned long long rec_key(const Rec64 *__restrict__ pk, uint32_t beg, uint32_t e) {
-    const uint32_t i = __ldg(&pk[beg + e].c.y);
-    return ((unsigned long long)(i + 1u) << 32) | e;
+// The 32 largest keys seen so far across the warp (ascending, lane 31 the
+// largest) after one more key per lane (0: none; real keys are nonzero).
+__device__ __forceinline__ unsigned long long warp_top32(unsigned long long top, unsigned long long key) {
+    key = warp_sort_asc(key);
+    const unsigned long long rev = __shfl_sync(0xffffffffu, key, 31 - (threadIdx.x & 31));
+    return warp_merge_asc(max(top, rev));
+}
+
+// Shared memory of the commit kernel (dynamic; kCommitCap records a round).
+struct CommitSmem {
+    uint32_t *idx;      // [cap] batch index of round record k
+    uint32_t *src;      // [cap] its bucket position within the cell
+    uint16_t *tick;     // [cap] its arrival rank within its pixel in this round
+    uint8_t *lp;        // [cap] its cell pixel
+    uint32_t *sidx;     // [cap] batch indices in pixel order (sorted position u)
+    uint32_t *ssrc;     // [cap] bucket positions in pixel order
+    uint8_t *slp;       // [cap] cell pixels in pixel order
+    uint32_t *total;    // [kCellPix] the batch's records per pixel
+    uint32_t *count;    // [kCellPix] this round's records per pixel
+    uint32_t *start;    // [kCellPix] first sorted position of each pixel in this round
+    uint32_t *state;    // [kCellPix] queue state of each pixel before the batch
+    uint32_t *misc;     // [2] records gathered in this round, end of this round's pixels
+};
+
+constexpr size_t kCommitSmemBytes =
+    (size_t)kCommitCap * (4 + 4 + 2 + 1 + 4 + 4 + 1) + (size_t)kCellPix * 16 + 16;
+
+__device__ __forceinline__ CommitSmem commit_smem(unsigned char *base) {
+    CommitSmem m;
+    unsigned char *p = base;
+    auto take = [&](size_t bytes) {
+        unsigned char *r = p;
+        p += (bytes + 15) & ~(size_t)15;
+        return r;
+    };
+    m.idx = reinterpret_cast<uint32_t *>(take(4 * kCommitCap));
+    m.src = reinterpret_cast<uint32_t *>(take(4 * kCommitCap));
+    m.sidx = reinterpret_cast<uint32_t *>(take(4 * kCommitCap));
+    m.ssrc = reinterpret_cast<uint32_t *>(take(4 * kCommitCap));
+    m.total = reinterpret_cast<uint32_t *>(take(4 * kCellPix));
+    m.count = reinterpret_cast<uint32_t *>(take(4 * kCellPix));
+    m.start = reinterpret_cast<uint32_t *>(take(4 * kCellPix));
+    m.state = reinterpret_cast<uint32_t *>(take(4 * kCellPix));
+    m.misc = reinterpret_cast<uint32_t *>(take(16));
+    m.tick = reinterpret_cast<uint16_t *>(take(2 * kCommitCap));
+    m.lp = reinterpret_cast<uint8_t *>(take(kCommitCap));
+    m.slp = reinterpret_cast<uint8_t *>(take(kCommitCap));
+    return m;
+}
+
+constexpr int kCommitUnroll = 4;   // bucket records in flight per thread (gather)
+constexpr int kPutUnroll = 2;      // kept records in flight per thread (queue writes)
+
+// Writes kept records (bucket position src, queue slot dst, sequence number)
+// field by field, the loads of each field issued together.
+template <int CT>
+__device__ __forceinline__ void put_entries(const Bucket &bk, uint32_t c0, const uint32_t (&src)[kPutUnroll],
+                                            const size_t (&dst)[kPutUnroll], const uint32_t (&seq)[kPutUnroll],
+                                            const Queues &q) {
+    uint4 a[kPutUnroll], q1[kPutUnroll];
+#pragma unroll
+    for (int r = 0; r < kPutUnroll; ++r)
+        if (src[r] != kInvalid) {
+            a[r] = bk.r[4 * (size_t)(c0 + src[r])];
+            q1[r] = bk.r[4 * (size_t)(c0 + src[r]) + 1];
+        }
+#pragma unroll
+    for (int r = 0; r < kPutUnroll; ++r)
+        if (src[r] != kInvalid) {
+            q.xy[dst[r]] = make_float2(__uint_as_float(a[r].x), __uint_as_float(a[r].y));
+            q.t[dst[r]] = __uint_as_float(a[r].z);
+            q.depth[dst[r]] = __uint_as_float(a[r].w);
+            q.seq[dst[r]] = seq[r];
+        }
+    uint4 bb[kPutUnroll];
+#pragma unroll
+    for (int r = 0; r < kPutUnroll; ++r)
+        if (src[r] != kInvalid) bb[r] = bk.r[4 * (size_t)(c0 + src[r]) + 2];
+#pragma unroll
+    for (int r = 0; r < kPutUnroll; ++r)
+        if (src[r] != kInvalid) {
+            if (CT == AFR_F32) {
+                reinterpret_cast<float4 *>(q.col)[dst[r]] =
+                    make_float4(__uint_as_float(bb[r].x), __uint_as_float(bb[r].y), __uint_as_float(bb[r].z), 0.f);
+                q.mo[dst[r]] = make_float2(__uint_as_float(bb[r].w), __uint_as_float(q1[r].y));
+            } else {
+                reinterpret_cast<ushort4 *>(q.col)[dst[r]] =
+                    make_ushort4((unsigned short)(bb[r].x & 0xFFFFu), (unsigned short)(bb[r].x >> 16),
+                                 (unsigned short)bb[r].y, 0);
+                q.mo[dst[r]] = make_float2(__uint_as_float(bb[r].z), __uint_as_float(bb[r].w));
+            }
+            if (q.world) {
+                const uint4 q3 = bk.r[4 * (size_t)(c0 + src[r]) + 3];
+                q.world[dst[r]] = make_float4(__uint_as_float(q1[r].z), __uint_as_float(q1[r].w),
+                                              __uint_as_float(q3.x), 0.f);
+            }
+        }
 }
 
 template <int CT>
-__global__ void __launch_bounds__(256) k_commit(const uint32_t *__restrict__ poff, int P, int b, uint32_t seq0,
-                                                const Rec64 *__restrict__ pk, float2 *__restrict__ r_xy,
-                                                float2 *__restrict__ r_mo, float *__restrict__ r_t,
-                                                float *__restrict__ r_depth, uint32_t *__restrict__ r_seq,
-                                                void *__restrict__ r_col, uint32_t *__restrict__ r_state,
-                                                float4 *__restrict__ r_world) {
-    using Codec = RecCodec<CT>;
-    const int lane = threadIdx.x & 31;
-    const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < P; p += warps) {
-        const uint32_t beg = poff[p], m = poff[p + 1] - beg;
-        if (m == 0) continue;
-        const uint32_t st = r_state[p];
-        const uint32_t c0 = st & 0xFFFFu, h0 = st >> 16;
-        const uint32_t kept = m < (uint32_t)b ? m : (uint32_t)b;
-        if (lane == 0) {
-            const uint32_t cn = (uint64_t)c0 + m < (uint64_t)b ? c0 + m : (uint32_t)b;
-            const uint32_t hn = (uint32_t)((h0 + (uint64_t)m) % (uint32_t)b);
-            r_state[p] = cn | (hn << 16);
+__global__ void __launch_bounds__(kCommitThreads, 2) k_cell_commit(const uint32_t *__restrict__ coff, int W, int H,
+                                                                   int ncx, int b, uint32_t seq0, Bucket bk, Queues q) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const CommitSmem sm = commit_smem(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t cell = blockIdx.x;
+    const uint32_t c0 = coff[cell * kSubBuckets], nc = coff[(cell + 1) * kSubBuckets] - c0;
+    if (nc == 0) return;   // block-uniform
+    const int x0 = (int)(cell % (uint32_t)ncx) * kCellW, y0 = (int)(cell / (uint32_t)ncx) * kCellH;
+    const uint32_t ub = (uint32_t)b;
+    // image pixel of cell pixel l (inside the image for every l that holds a record)
+    auto pixel_of = [&](uint32_t l) -> size_t {
+        return (size_t)(y0 + (int)(l / kCellW)) * (size_t)W + (size_t)(x0 + (int)(l % kCellW));
+    };
+    // cell pixel of a bucket record, kCellPix for a dead record
+    auto local_of = [&](uint32_t i, uint4 a) -> uint32_t {
+        if (i == kInvalid) return kCellPix;
+        return (uint32_t)(((int)floorf(__uint_as_float(a.y)) - y0) * kCellW + ((int)floorf(__uint_as_float(a.x)) - x0));
+    };
+    const bool multi = nc > (uint32_t)kCommitCap;
+    for (int l = tid; l < kCellPix; l += kCommitThreads) {
+        const int x = x0 + l % kCellW, y = y0 + l / kCellW;
+        sm.state[l] = (x < W && y < H) ? q.state[(size_t)y * W + x] : 0u;
+        sm.total[l] = 0;
+    }
+    __syncthreads();
+    if (multi) {
+        // per-pixel totals, to group the pixels into rounds
+        for (uint32_t j = tid; j < nc; j += kCommitThreads) {
+            const uint32_t l = local_of(bk.r[4 * (size_t)(c0 + j) + 1].x, bk.r[4 * (size_t)(c0 + j)]);
+            if (l < kCellPix) atomicAdd(&sm.total[l], 1u);
         }
-        if (m <= 32) {
-            // lane k holds record k; its rank in insertion order is the number
-            // of the pixel's records with a smaller batch index (indices are unique)
-            Rec64 rec;
-            uint32_t i = 0xFFFFFFFFu;
-            if (lane < (int)m) {
-                rec.a = __ldg(&pk[beg + lane].a);
-                rec.b = __ldg(&pk[beg + lane].b);
-                rec.c = __ldg(&pk[beg + lane].c);
-                i = rec.c.y;
+        __syncthreads();
+        // a pixel alone above one round: a warp streams the bucket
+        for (int l = warp; l < kCellPix; l += kCommitWarps) {
+            const uint32_t m = sm.total[l];
+            if (m <= (uint32_t)kCommitCap) continue;
+            unsigned long long top = 0ull;
+            for (uint32_t base = 0; base < nc; base += 32) {
+                const uint32_t j = base + (uint32_t)lane;
+                unsigned long long key = 0ull;
+                if (j < nc) {
+                    const uint32_t i = bk.r[4 * (size_t)(c0 + j) + 1].x;
+                    if (local_of(i, bk.r[4 * (size_t)(c0 + j)]) == (uint32_t)l)
+                        key = ((unsigned long long)(i + 1u) << 32) | j;
+                }
+                top = warp_top32(top, key);
             }
-            uint32_t rank = 0;
-            for (uint32_t k = 0; k < m; ++k) rank += __shfl_sync(0xffffffffu, i, k) < i;
-            if (lane < (int)m && rank >= m - kept) {
-                const uint32_t s = (h0 + rank) % (uint32_t)b;
-                const size_t dst = (size_t)p * b + s;
-                r_xy[dst] = make_float2(__uint_as_float(rec.a.x), __uint_as_float(rec.a.y));
-                r_t[dst] = __uint_as_float(rec.a.z);
-                r_depth[dst] = __uint_as_float(rec.a.w);
-                r_mo[dst] = Codec::motion(rec.b, rec.c);
-                r_seq[dst] = seq0 + i;
-                reinterpret_cast<typename Codec::T *>(r_col)[dst] = Codec::color(rec.b, rec.c);
-                if (r_world) {
-                    const uint4 d = __ldg(&pk[beg + lane].d);
-                    r_world[dst] = make_float4(__uint_as_float(d.x), __uint_as_float(d.y), __uint_as_float(d.z), 0.f);
+            const uint32_t kept = min(m, ub);
+            uint32_t src[kPutUnroll], seq[kPutUnroll];
+#pragma unroll
+            for (int r = 0; r < kPutUnroll; ++r) src[r] = kInvalid;
+            size_t dst[kPutUnroll];
+            if (lane >= 32 - (int)kept) {
+                const uint32_t rank = m - 32u + (uint32_t)lane;   // position in insertion order
+                src[0] = (uint32_t)top;
+                seq[0] = seq0 + (uint32_t)(top >> 32) - 1u;
+                dst[0] = pixel_of(l) * ub + ((sm.state[l] >> 16) + rank) % ub;
+            }
+            put_entries<CT>(bk, c0, src, dst, seq, q);
+        }
+    }
+    uint32_t group_begin = 0;
+    while (group_begin < (uint32_t)kCellPix) {
+        if (tid == 0) {
+            uint32_t e = kCellPix;
+            if (multi) {
+                uint32_t acc = 0;
+                for (e = group_begin; e < (uint32_t)kCellPix; ++e) {
+                    const uint32_t m = sm.total[e];
+                    if (m > (uint32_t)kCommitCap) continue;   // streamed above
+                    if (acc + m > (uint32_t)kCommitCap) break;
+                    acc += m;
                 }
             }
-            continue;
+            sm.misc[1] = e;
+            sm.misc[0] = 0;
         }
-        // more than 32: the 32 newest by chunked bitonic top-32 (0 marks an
-        // empty lane and sorts first)
-        unsigned long long key = lane < (int)m ? rec_key(pk, beg, lane) : 0ull;
-        key = warp_sort_asc(key);
-        for (uint32_t c = 32; c < m; c += 32) {
-            unsigned long long k2 = c + lane < m ? rec_key(pk, beg, c + lane) : 0ull;
-            k2 = warp_sort_asc(k2);
-            const unsigned long long rev = __shfl_sync(0xffffffffu, k2, 31 - lane);
-            key = warp_merge_asc(max(key, rev));   // the 32 largest so far, ascending
-        }
-        if (lane >= 32 - (int)kept) {
-            const uint32_t i = (uint32_t)(key >> 32) - 1u;
-            const Rec64 &rec = pk[beg + (uint32_t)key];
-            const uint4 ra = rec.a, rb = rec.b, rc = rec.c;
-            const uint32_t rank = m - 32u + (uint32_t)lane;           // position in insertion order
-            const uint32_t s = (h0 + rank) % (uint32_t)b;
-            const size_t dst = (size_t)p * b + s;
-            r_xy[dst] = make_float2(__uint_as_float(ra.x), __uint_as_float(ra.y));
-            r_t[dst] = __uint_as_float(ra.z);
-            r_depth[dst] = __uint_as_float(ra.w);
-            r_mo[dst] = Codec::motion(rb, rc);
-            r_seq[dst] = seq0 + i;
-            reinterpret_cast<typename Codec::T *>(r_col)[dst] = Codec::color(rb, rc);
-            if (r_world) {
-                const uint4 d = rec.d;
-                r_world[dst] = make_float4(__uint_as_float(d.x), __uint_as_float(d.y), __uint_as_float(d.z), 0.f);
+        for (int l = tid; l < kCellPix; l += kCommitThreads) sm.count[l] = 0;
+        __syncthreads();
+        const uint32_t ge = sm.misc[1];
+        // gather the round's records, kCommitUnroll bucket loads in flight per
+        // thread; a single round keeps record j at place j (dead ones unused)
+        for (uint32_t base = 0; base < nc; base += kCommitThreads * kCommitUnroll) {
+            uint32_t ii[kCommitUnroll];
+            uint4 aa[kCommitUnroll];
+#pragma unroll
+            for (int r = 0; r < kCommitUnroll; ++r) {
+                const uint32_t j = base + tid + r * kCommitThreads;
+                ii[r] = kInvalid;
+                if (j < nc) {
+                    aa[r] = bk.r[4 * (size_t)(c0 + j)];
+                    ii[r] = bk.r[4 * (size_t)(c0 + j) + 1].x;
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < kCommitUnroll; ++r) {
+                const uint32_t j = base + tid + r * kCommitThreads;
+                const uint32_t l = local_of(ii[r], aa[r]);
+                // a single round marks every place: src[j] == j for a record
+                // gathered at j, kInvalid for a dead record (shared memory
+                // holds earlier blocks' values otherwise)
+                if (!multi && j < nc && l == kCellPix) sm.src[j] = kInvalid;
+                if (l < group_begin || l >= ge || (multi && sm.total[l] > (uint32_t)kCommitCap)) continue;
+                const uint32_t k = multi ? atomicAdd(&sm.misc[0], 1u) : j;
+                sm.idx[k] = ii[r];
+                sm.src[k] = j;
+                sm.lp[k] = (uint8_t)l;
+                sm.tick[k] = (uint16_t)atomicAdd(&sm.count[l], 1u);
             }
         }
+        __syncthreads();
+        if (warp == 0) {   // exclusive scan of the counts (128 = 4 per lane)
+            uint32_t v[4], sum = 0;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                v[r] = sm.count[lane * 4 + r];
+                sum += v[r];
+            }
+            uint32_t incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            uint32_t run = incl - sum;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                sm.start[lane * 4 + r] = run;
+                run += v[r];
+            }
+            if (lane == 31) sm.misc[0] = run;   // the round's records
+        }
+        if (!multi)
+            for (int l = tid; l < kCellPix; l += kCommitThreads) sm.total[l] = sm.count[l];
+        __syncthreads();
+        const uint32_t nr = sm.misc[0];
+        // copies of the round's records in pixel order
+        if (multi) {
+            for (uint32_t k = tid; k < nr; k += kCommitThreads) {
+                const uint32_t l = sm.lp[k], u = sm.start[l] + sm.tick[k];
+                sm.sidx[u] = sm.idx[k];
+                sm.ssrc[u] = sm.src[k];
+                sm.slp[u] = (uint8_t)l;
+            }
+        } else {
+            for (uint32_t j = tid; j < nc; j += kCommitThreads) {
+                if (sm.src[j] != j) continue;   // a dead record's place
+                const uint32_t l = sm.lp[j], u = sm.start[l] + sm.tick[j];
+                sm.sidx[u] = sm.idx[j];
+                sm.ssrc[u] = j;
+                sm.slp[u] = (uint8_t)l;
+            }
+        }
+        __syncthreads();
+        // up to 32 records in a pixel: a thread per record counts the pixel's
+        // records with a smaller batch index (batch indices are unique)
+        for (uint32_t u0 = 0; u0 < nr; u0 += kCommitThreads * kPutUnroll) {
+            uint32_t src[kPutUnroll], seq[kPutUnroll];
+            size_t dst[kPutUnroll];
+#pragma unroll
+            for (int r = 0; r < kPutUnroll; ++r) {
+                const uint32_t u = u0 + tid + r * kCommitThreads;
+                src[r] = kInvalid;
+                if (u >= nr) continue;
+                const uint32_t l = sm.slp[u], m = sm.count[l];
+                if (m > 32u) continue;
+                const uint32_t beg = sm.start[l], me = sm.sidx[u];
+                uint32_t rank = 0;
+                for (uint32_t v = beg; v < beg + m; ++v) rank += sm.sidx[v] < me;
+                if (rank + min(m, ub) < m) continue;   // evicted by newer samples of the batch
+                src[r] = sm.ssrc[u];
+                seq[r] = seq0 + me;
+                dst[r] = pixel_of(l) * ub + ((sm.state[l] >> 16) + rank) % ub;
+            }
+            put_entries<CT>(bk, c0, src, dst, seq, q);
+        }
+        // more than 32: a warp keeps the newest 32 by bitonic merges of the
+        // pixel's records, 32 at a time
+        for (uint32_t l = group_begin + (uint32_t)warp; l < ge; l += kCommitWarps) {
+            const uint32_t m = sm.count[l];
+            if (m <= 32u) continue;
+            const uint32_t beg = sm.start[l];
+            unsigned long long top = 0ull;
+            for (uint32_t base = 0; base < m; base += 32) {
+                unsigned long long key = 0ull;
+                if (base + (uint32_t)lane < m) {
+                    const uint32_t u = beg + base + lane;
+                    key = ((unsigned long long)(sm.sidx[u] + 1u) << 32) | u;
+                }
+                top = warp_top32(top, key);
+            }
+            const uint32_t kept = min(m, ub);
+            uint32_t src[kPutUnroll], seq[kPutUnroll];
+#pragma unroll
+            for (int r = 0; r < kPutUnroll; ++r) src[r] = kInvalid;
+            size_t dst[kPutUnroll];
+            if (lane >= 32 - (int)kept) {
+                const uint32_t u = (uint32_t)top, rank = m - 32u + (uint32_t)lane;
+                src[0] = sm.ssrc[u];
+                seq[0] = seq0 + sm.sidx[u];
+                dst[0] = pixel_of(l) * ub + ((sm.state[l] >> 16) + rank) % ub;
+            }
+            put_entries<CT>(bk, c0, src, dst, seq, q);
+        }
+        __syncthreads();
+        group_begin = ge;
+    }
+    // queue states after pushing each pixel's records
+    for (int l = tid; l < kCellPix; l += kCommitThreads) {
+        const uint32_t m = sm.total[l];
+        if (m == 0) continue;
+        const uint32_t st = sm.state[l], cnt = st & 0xFFFFu, h = st >> 16;
+        const uint32_t cn = (uint64_t)cnt + m < (uint64_t)ub ? cnt + m : ub;
+        const uint32_t hn = (uint32_t)((h + (uint64_t)m) % ub);
+        q.state[pixel_of((uint32_t)l)] = cn | (hn << 16);
     }
 }
 
 template <int CT>
 cudaError_t run(AfrContext *c, const float4 *pos, const void *col, const float2 *mo, const float4 *world, uint32_t n,
                 uint32_t seq0, cudaStream_t s) {
-    Rec64 *pk = reinterpret_cast<Rec64 *>(c->pack);
-    cudaError_t e = cudaMemsetAsync(c->pcnt, 0, sizeof(uint32_t) * c->P, s);
-    if (e != cudaSuccess) return e;
+    const int ncx = (c->W + kCellW - 1) / kCellW;
+    const int nkeys = c->ncells * kSubBuckets;
+    Bucket bk{c->bucket, c->r_world != nullptr};
+    static bool attr_set = false;   // per colour type: raise the commit kernel's shared-memory limit once
+    cudaError_t e = cudaSuccess;
+    if (!attr_set) {
+        e = cudaFuncSetAttribute(k_cell_commit<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kCommitSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if ((e = cudaMemsetAsync(c->ccnt, 0, sizeof(uint32_t) * nkeys, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->ccur, 0, sizeof(uint32_t) * nkeys, s)) != cudaSuccess) return e;
     const int g = grid_for(n, 256);
-    k_hist<CT><<<g, 256, 0, s>>>(pos, col, mo, n, c->W, c->H, c->bin_of, c->pcnt, c->dcount);
-    if ((e = scan_exclusive(c->pcnt, c->poff, c->P, c->scan_tmp, s)) != cudaSuccess) return e;
-    k_place<CT><<<grid_for(n, 32 * kPlaceWarps), 32 * kPlaceWarps, 0, s>>>(pos, col, mo, n, c->bin_of, c->poff,
-                                                                          c->r_world ? world : nullptr, pk);
-    const int gc = grid_for((size_t)c->P * 32, 256);
-    k_commit<CT><<<gc, 256, 0, s>>>(c->poff, c->P, c->b, seq0, pk, c->r_xy, c->r_mo, c->r_t, c->r_depth, c->r_seq,
-                                    c->r_col, c->r_state, c->r_world);
+    k_cell_count<<<g, 256, 0, s>>>(pos, n, c->W, c->H, ncx, c->ccnt);
+    if ((e = scan_exclusive(c->ccnt, c->coff, nkeys, c->scan_tmp, s)) != cudaSuccess) return e;
+    const int gs = grid_for((n + kScatterUnroll - 1) / kScatterUnroll, 32 * kScatterWarps);
+    k_cell_scatter<CT><<<gs, 32 * kScatterWarps, 0, s>>>(pos, col, mo, world, n, c->W, c->H, ncx, c->coff, c->ccur,
+                                                          bk, c->fifo_n ? c->fifo_flag : nullptr, c->dcount);
+    Queues q{c->r_xy, c->r_mo, c->r_t, c->r_depth, c->r_seq, c->r_col, c->r_state, c->r_world};
+    k_cell_commit<CT><<<c->ncells, kCommitThreads, kCommitSmemBytes, s>>>(c->coff, c->W, c->H, ncx, c->b, seq0, bk, q);
     return cudaGetLastError();
 }
 
+}  // namespace
+
+int ingest_sub_buckets() { return kSubBuckets; }
+
+namespace {
+
 // ---- reconstructor queue (section 5.2) ----------------------------------------
-// The batch's accepted samples (k_hist marked the rejected ones) enter the
+// The batch's accepted samples (the scatter flagged them) enter the
 // N-slot queue in index order: a scan gives each its rank r among the
 // batch's accepted samples, and it lands at slot (total + r) mod N; of a batch
 // with more than N accepted samples only the last N are written.
-__global__ void __launch_bounds__(256) k_fifo_flag(const uint2 *__restrict__ bin_of, uint32_t n,
-                                                   uint32_t *__restrict__ flag) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        flag[i] = bin_of[i].x != kInvalid ? 1u : 0u;
-}
-
 template <int CT>
 __global__ void __launch_bounds__(256) k_fifo_append(const float4 *__restrict__ pos, const void *__restrict__ col,
                                                      const float2 *__restrict__ mo, uint32_t n,
@@ -314,7 +585,6 @@ template <int CT>
 cudaError_t run_fifo(AfrContext *c, const float4 *pos, const void *col, const float2 *mo, const float4 *world,
                      uint32_t n, uint32_t seq0, cudaStream_t s) {
     const int g = grid_for(n, 256);
-    k_fifo_flag<<<g, 256, 0, s>>>(c->bin_of, n, c->fifo_flag);
     cudaError_t e = scan_exclusive(c->fifo_flag, c->fifo_rank, n, c->fifo_scan, s);
     if (e != cudaSuccess) return e;
     k_fifo_append<CT><<<g, 256, 0, s>>>(pos, col, mo, n, c->fifo_flag, c->fifo_rank, seq0, (uint32_t)c->fifo_n,
@@ -337,8 +607,6 @@ cudaError_t launch_fifo_append(AfrContext *c, const AfrSampleBatch *batch, uint3
         default: return run_fifo<AFR_BF16>(c, pos, batch->color_dev, mo, world, n, seq0, s);
     }
 }
-
-size_t packed_bytes(int) { return sizeof(Rec64); }
 
 cudaError_t launch_ingest(AfrContext *c, const AfrSampleBatch *batch, uint32_t n, uint32_t seq0,
                           cudaStream_t s) {

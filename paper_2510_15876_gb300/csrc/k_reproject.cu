@@ -1,17 +1,23 @@
 // k_reproject.cu -- section 6.2: move every buffered sample to the display
 // time along its screen velocity and rebin it into the frame view (a CSR
-// over destination pixels).
+// over destination pixels), ordered within each bin by sequence number.
 //
-//  count:   thread per queue slot; x' = x + m_x (t_now - t) with one rounding
-//           per operation (__fmul_rn / __fadd_rn, so no contraction), drops
-//           samples leaving the image, counts per destination bin (warp-
-//           aggregated) and keeps the smallest a^2 per bin (the filter's
-//           exponent shift).
-//  scan:    bin offsets.
-//  scatter: same slot walk, writes (x', y', a^2, bin column) with the colour
-//           and the sequence number at the bin's next free record.
-//  order:   each record finds its rank by sequence number within its bin, so
-//           that the frame view, and every sum over it, is deterministic.
+//  count:  thread per queue slot; x' = x + m_x (t_now - t) with one rounding
+//          per operation (__fmul_rn / __fadd_rn, so no contraction), drops
+//          samples leaving the image, counts per destination bin (warp-
+//          aggregated) and keeps the smallest a^2 per bin (the filter's
+//          exponent shift).
+//  scan:   bin offsets.
+//  list:   same slot walk; each moved sample writes its slot index into its
+//          bin's list (unordered, 4 bytes a sample).
+//  place:  thread per frame record, in bin order: the slot of list entry e
+//          is moved again, its rank in the bin is the number of the bin's
+//          slots with a smaller sequence number (sequence numbers are
+//          unique), and it writes (x', y', a^2, bin column), its colour and its
+//          sequence number to the bin's offset + rank. The lanes of a warp
+//          mostly share a bin, so the rank scans are broadcast reads and the
+//          record writes cover whole sectors; the frame view, and every sum
+//          over it, is deterministic without a reorder pass over the records.
 #include "afr_internal.cuh"
 
 namespace afr {
@@ -126,65 +132,71 @@ __global__ void __launch_bounds__(256) k_count(uint32_t nslots, int b, int bshif
     }
 }
 
-template <int CT, bool FIFO, bool CAM>
-__global__ void __launch_bounds__(256) k_scatter(uint32_t nslots, int b, int bshift, int W, int H, float t_now,
-                                                 Camera cam, const float4 *__restrict__ world,
-                                                 const uint32_t *__restrict__ state, const float2 *__restrict__ r_xy,
-                                                 const float2 *__restrict__ r_mo, const float *__restrict__ r_t,
-                                                 const uint32_t *__restrict__ r_seq, const void *__restrict__ r_col,
-                                                 const uint32_t *__restrict__ foff, uint32_t *__restrict__ fcur,
-                                                 float4 *__restrict__ fpos, void *__restrict__ fcol,
-                                                 uint32_t *__restrict__ fseq) {
-    using CS = ColorStore<CT>;
+// The slot walk shared by the list and place passes: the moved sample of
+// live slot i, or !ok.
+template <bool FIFO, bool CAM>
+__device__ __forceinline__ bool live_move(uint32_t i, uint32_t nlive, int b, int bshift, int W, int H, float t_now,
+                                          const Camera &cam, const float4 *__restrict__ world,
+                                          const uint32_t *__restrict__ state, const float2 *__restrict__ r_xy,
+                                          const float2 *__restrict__ r_mo, const float *__restrict__ r_t, Moved &mv) {
+    if (FIFO) {
+        if (i >= nlive) return false;
+    } else {
+        uint32_t p;
+        int s;
+        split_slot(i, b, bshift, p, s);
+        if (!slot_live(__ldg(state + p), s, b)) return false;
+    }
+    mv = CAM ? move_camera(__ldg(world + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H, cam)
+             : move_sample(__ldg(r_xy + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H);
+    return mv.ok;
+}
+
+template <bool FIFO, bool CAM>
+__global__ void __launch_bounds__(256) k_list(uint32_t nslots, int b, int bshift, int W, int H, float t_now,
+                                              Camera cam, const float4 *__restrict__ world,
+                                              const uint32_t *__restrict__ state, const float2 *__restrict__ r_xy,
+                                              const float2 *__restrict__ r_mo, const float *__restrict__ r_t,
+                                              const uint32_t *__restrict__ foff, uint32_t *__restrict__ fcur,
+                                              uint32_t *__restrict__ flist) {
     const uint32_t nlive = FIFO ? min(__ldg(state), nslots) : 0u;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nslots; i += gridDim.x * blockDim.x) {
-        if (FIFO) {
-            if (i >= nlive) continue;
-        } else {
-            uint32_t p;
-            int s;
-            split_slot(i, b, bshift, p, s);
-            if (!slot_live(__ldg(state + p), s, b)) continue;
-        }
-        Moved mv = CAM ? move_camera(__ldg(world + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H, cam)
-                       : move_sample(__ldg(r_xy + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H);
-        if (!mv.ok) continue;
-        uint32_t e = __ldg(foff + mv.bin) + agg_inc(fcur, mv.bin);
-        fpos[e] = make_float4(mv.xp, mv.yp, mv.a2, __int_as_float((int)floorf(mv.xp)));
-        reinterpret_cast<typename CS::T *>(fcol)[e] = CS::raw(r_col, i);
-        fseq[e] = __ldg(r_seq + i);
+        Moved mv;
+        if (!live_move<FIFO, CAM>(i, nlive, b, bshift, W, H, t_now, cam, world, state, r_xy, r_mo, r_t, mv)) continue;
+        flist[__ldg(foff + mv.bin) + agg_inc(fcur, mv.bin)] = i;
     }
 }
 
-// Orders the records of each bin by sequence number: one thread per record
-// counts the records of its bin with a smaller sequence number (sequence
-// numbers are unique) and moves its record there. Bins holding more than
-// kSortedBinMax records keep arrival order and are counted.
-template <int CT>
-__global__ void __launch_bounds__(256) k_order(int W, const uint32_t *__restrict__ foff, uint32_t P,
-                                               const float4 *__restrict__ src_pos, const void *__restrict__ src_col,
-                                               const uint32_t *__restrict__ src_seq, float4 *__restrict__ dst_pos,
-                                               void *__restrict__ dst_col, uint32_t *__restrict__ dst_seq,
+// fcnt holds every bin's count here; a bin above kSortedBinMax records takes
+// its ranks by counting fcnt down (arrival order) and is counted as unsorted.
+template <int CT, bool FIFO, bool CAM>
+__global__ void __launch_bounds__(256) k_place(int W, int H, float t_now, Camera cam, const float4 *__restrict__ world,
+                                               const float2 *__restrict__ r_xy, const float2 *__restrict__ r_mo,
+                                               const float *__restrict__ r_t, const uint32_t *__restrict__ r_seq,
+                                               const void *__restrict__ r_col, uint32_t P,
+                                               const uint32_t *__restrict__ foff, const uint32_t *__restrict__ flist,
+                                               uint32_t *__restrict__ fcnt, float4 *__restrict__ fpos,
+                                               void *__restrict__ fcol, uint32_t *__restrict__ fseq,
                                                unsigned long long *__restrict__ dcount) {
     using CS = ColorStore<CT>;
-    using T = typename CS::T;
     const uint32_t n = __ldg(foff + P);
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        float4 r = src_pos[e];
-        uint32_t bin = (uint32_t)(int)floorf(r.y) * (uint32_t)W + (uint32_t)__float_as_int(r.w);
-        uint32_t beg = __ldg(foff + bin), end = __ldg(foff + bin + 1);
-        uint32_t sq = src_seq[e];
-        uint32_t dst = e;
+        const uint32_t i = __ldg(flist + e);
+        const Moved mv = CAM ? move_camera(__ldg(world + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H, cam)
+                             : move_sample(__ldg(r_xy + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H);
+        const uint32_t sq = __ldg(r_seq + i);
+        const uint32_t beg = __ldg(foff + mv.bin), end = __ldg(foff + mv.bin + 1);
+        uint32_t rank = 0;
         if (end - beg <= (uint32_t)kSortedBinMax) {
-            uint32_t rank = 0;
-            for (uint32_t k = beg; k < end; ++k) rank += __ldg(src_seq + k) < sq;
-            dst = beg + rank;
-        } else if (e == beg) {
-            atomicAdd(dcount + CNT_UNSORTED, 1ull);
+            for (uint32_t k = beg; k < end; ++k) rank += __ldg(r_seq + __ldg(flist + k)) < sq;
+        } else {
+            rank = atomicSub(fcnt + mv.bin, 1u) - 1u;
+            if (rank == 0) atomicAdd(dcount + CNT_UNSORTED, 1ull);
         }
-        dst_pos[dst] = r;
-        reinterpret_cast<T *>(dst_col)[dst] = reinterpret_cast<const T *>(src_col)[e];
-        dst_seq[dst] = sq;
+        const uint32_t d = beg + rank;
+        fpos[d] = make_float4(mv.xp, mv.yp, mv.a2, __int_as_float((int)floorf(mv.xp)));
+        reinterpret_cast<typename CS::T *>(fcol)[d] = CS::raw(r_col, i);
+        fseq[d] = sq;
     }
 }
 
@@ -223,22 +235,23 @@ cudaError_t launch_reproject(AfrContext *c, float t_now, const Camera *camp, cud
 #undef AFR_COUNT
     if ((e = scan_exclusive(c->fcnt, c->foff, c->P, c->scan_tmp, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->fcnt, 0, sizeof(uint32_t) * c->P, s)) != cudaSuccess) return e;
-    // records land unordered in the second half of the buffers, then k_order
-    // writes them ordered into the first half
-    float4 *tmp_pos = c->fpos + c->frame_cap;
-    void *tmp_col = static_cast<char *>(c->fcol) + c->frame_cap * c->csize;
-    uint32_t *tmp_seq = c->fseq + c->frame_cap;
-#define AFR_SCATTER(CT_, F_, C_)                                                                              \
-    k_scatter<CT_, F_, C_><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, cm, wp, state, xy, mo, tt, sq, col, \
-                                             c->foff, c->fcnt, tmp_pos, tmp_col, tmp_seq)
+#define AFR_LIST(F_, C_)                                                                                       \
+    k_list<F_, C_><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, cm, wp, state, xy, mo, tt, c->foff,  \
+                                     c->fcnt, c->flist)
+    if (fifo && cam) AFR_LIST(true, true);
+    else if (fifo) AFR_LIST(true, false);
+    else if (cam) AFR_LIST(false, true);
+    else AFR_LIST(false, false);
+#undef AFR_LIST
+#define AFR_PLACE(CT_, F_, C_)                                                                                     \
+    k_place<CT_, F_, C_><<<g, 256, 0, s>>>(c->W, c->H, t_now, cm, wp, xy, mo, tt, sq, col, (uint32_t)c->P, c->foff, \
+                                           c->flist, c->fcnt, c->fpos, c->fcol, c->fseq, c->dcount)
 #define AFR_REPROJ(CT_)                                                                                        \
     do {                                                                                                       \
-        if (fifo && cam) AFR_SCATTER(CT_, true, true);                                                         \
-        else if (fifo) AFR_SCATTER(CT_, true, false);                                                          \
-        else if (cam) AFR_SCATTER(CT_, false, true);                                                           \
-        else AFR_SCATTER(CT_, false, false);                                                                   \
-        k_order<CT_><<<g, 256, 0, s>>>(c->W, c->foff, (uint32_t)c->P, tmp_pos, tmp_col, tmp_seq, c->fpos, c->fcol, \
-                                       c->fseq, c->dcount);                                                    \
+        if (fifo && cam) AFR_PLACE(CT_, true, true);                                                           \
+        else if (fifo) AFR_PLACE(CT_, true, false);                                                            \
+        else if (cam) AFR_PLACE(CT_, false, true);                                                             \
+        else AFR_PLACE(CT_, false, false);                                                                     \
     } while (0)
     switch (c->ct) {
         case AFR_F32: AFR_REPROJ(AFR_F32); break;
@@ -246,7 +259,7 @@ cudaError_t launch_reproject(AfrContext *c, float t_now, const Camera *camp, cud
         default: AFR_REPROJ(AFR_BF16); break;
     }
 #undef AFR_REPROJ
-#undef AFR_SCATTER
+#undef AFR_PLACE
     return cudaGetLastError();
 }
 

@@ -12,7 +12,9 @@
 //
 // The scratch address is looked up with cudaGetSymbolAddress once per device,
 // on the first call made with that device current, and cached; make that
-// first call before any stream capture. Every call shares the array and
+// first call before any stream capture. The cache is not refreshed after
+// cudaDeviceReset (the module may then load at another address), so calls
+// made after a device reset are undefined. Every call shares the array and
 // leaves its contents behind, so each call clears the counters it uses first;
 // calls whose work overlaps on the GPU (other streams, or other host threads)
 // race on the array and must be serialised by the caller.
@@ -70,45 +72,53 @@ __global__ void __launch_bounds__(256) k_st_count(const float4 *pos, const void 
     }
 }
 
+// Each moved sample writes its batch index into its bin's list (unordered),
+// in seq_out, which the fix-up pass overwrites with the ordered indices.
 template <int CT>
-__global__ void __launch_bounds__(256) k_st_scatter(const float4 *pos, const void *col, const float2 *mo, uint32_t n,
-                                                    int W, int H, float t_now, const uint32_t *off, uint32_t *cur,
-                                                    float4 *out_rec, void *out_col, uint32_t *out_seq) {
+__global__ void __launch_bounds__(256) k_st_list(const float4 *pos, const void *col, const float2 *mo, uint32_t n,
+                                                 int W, int H, float t_now, const uint32_t *off, uint32_t *cur,
+                                                 uint32_t *list) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float4 rec;
+        uint32_t bin;
+        if (accept_and_move<CT>(pos, col, mo, i, W, H, t_now, rec, bin)) list[off[bin] + agg_inc(cur, bin)] = i;
+    }
+}
+
+// A sample's rank in its bin is the number of batch indices in the bin's list
+// below its own, so the records land in batch order; a bin above
+// kSortedBinMax records takes ranks by counting its counter down (arrival
+// order). The record's fourth lane holds the batch index until the fix-up.
+template <int CT>
+__global__ void __launch_bounds__(256) k_st_place(const float4 *pos, const void *col, const float2 *mo, uint32_t n,
+                                                  int W, int H, float t_now, const uint32_t *off, uint32_t *cnt,
+                                                  const uint32_t *list, float4 *out_rec, void *out_col) {
     using CS = ColorStore<CT>;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         float4 rec;
         uint32_t bin;
         if (!accept_and_move<CT>(pos, col, mo, i, W, H, t_now, rec, bin)) continue;
-        const uint32_t e = off[bin] + agg_inc(cur, bin);
-        out_rec[e] = rec;
-        reinterpret_cast<typename CS::T *>(out_col)[e] = CS::raw(col, i);
-        out_seq[e] = i;
+        const uint32_t beg = off[bin], end = off[bin + 1];
+        uint32_t rank = 0;
+        if (end - beg <= (uint32_t)kSortedBinMax) {
+            for (uint32_t k = beg; k < end; ++k) rank += list[k] < i;
+        } else {
+            rank = atomicSub(cnt + bin, 1u) - 1u;
+        }
+        rec.w = __uint_as_float(i);
+        out_rec[beg + rank] = rec;
+        reinterpret_cast<typename CS::T *>(out_col)[beg + rank] = CS::raw(col, i);
     }
 }
 
-// Orders each bin by batch index in place (insertion sort of its segment).
-template <int CT>
-__global__ void __launch_bounds__(256) k_st_order(uint32_t P, const uint32_t *off, float4 *rec, void *col,
-                                                  uint32_t *seq) {
-    using T = typename ColorStore<CT>::T;
-    T *c = reinterpret_cast<T *>(col);
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < P; q += gridDim.x * blockDim.x) {
-        const uint32_t beg = off[q], end = off[q + 1];
-        for (uint32_t k = beg + 1; k < end; ++k) {
-            const uint32_t sk = seq[k];
-            const float4 rk = rec[k];
-            const T ck = c[k];
-            uint32_t j = k;
-            while (j > beg && seq[j - 1] > sk) {
-                seq[j] = seq[j - 1];
-                rec[j] = rec[j - 1];
-                c[j] = c[j - 1];
-                --j;
-            }
-            seq[j] = sk;
-            rec[j] = rk;
-            c[j] = ck;
-        }
+// Moves each record's batch index to seq_out and puts the bin column back.
+__global__ void __launch_bounds__(256) k_st_fix(const uint32_t *off, uint32_t P, float4 *rec, uint32_t *seq) {
+    const uint32_t n = off[P];
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        float4 r = rec[e];
+        seq[e] = __float_as_uint(r.w);
+        r.w = __int_as_float((int)floorf(r.x));
+        rec[e] = r;
     }
 }
 
@@ -149,8 +159,11 @@ cudaError_t run_static(const AfrSampleBatch *b, uint32_t n, int W, int H, float 
     cudaError_t e = scan_exclusive(cnt, off, P, scan_tmp, s);
     if (e != cudaSuccess) return e;
     k_st_zero<<<gp, 256, 0, s>>>(cnt, P);
-    if (n) k_st_scatter<CT><<<gn, 256, 0, s>>>(pos, cin, mo, n, W, H, t_now, off, cnt, rec, col, seq);
-    k_st_order<CT><<<gp, 256, 0, s>>>(P, off, rec, col, seq);
+    if (n) {
+        k_st_list<CT><<<gn, 256, 0, s>>>(pos, cin, mo, n, W, H, t_now, off, cnt, seq);
+        k_st_place<CT><<<gn, 256, 0, s>>>(pos, cin, mo, n, W, H, t_now, off, cnt, seq, rec, col);
+        k_st_fix<<<gn, 256, 0, s>>>(off, P, rec, seq);
+    }
     if (n_frame) k_st_total<<<1, 1, 0, s>>>(off, P, n_frame);
     return cudaGetLastError();
 }

@@ -161,7 +161,10 @@ def test_fit_lowers_rms(c4, dev):
 @pytest.mark.parametrize("ct,max_tol", [("f16", 2e-3), ("bf16", None)])
 def test_precision_forms_against_fp64_oracle(dev, ct, max_tol):
     """A 1920 x 68 band of the 1080p workload (its samples only), colours
-    stored in 16 bits, against the FP64 oracle on the FP32 colours."""
+    stored in 16 bits. Compared with the FP64 oracle run on the FP32 source
+    colours (the error of the stored form: max and RMS per channel, FP16 gated
+    at 2e-3 on the max, BF16 reported) and with the FP64 oracle run on the
+    stored 16-bit colours (the error of the FP32 accumulation alone)."""
     from paper_2510_15876_gb300.api import Reconstructor, to_device_batch
     scene, batch = scenes.config_stream("c3_1920x1080x16", 0)
     W, band, y0 = scene.width, 68, 506
@@ -180,10 +183,22 @@ def test_precision_forms_against_fp64_oracle(dev, ct, max_tol):
     ref = oracle.reconstruct(ring)["image"][:, :3]
     err = np.abs(img - ref)
     mx, rms = err.max(axis=0), np.sqrt((err ** 2).mean(axis=0))
-    print(f"{ct}: max per channel {mx}, rms per channel {rms}")
+    stored = torch.from_numpy(sub["color"]).to(rec.color_dtype).float().numpy()
+    ring16 = oracle.Ring(W, band, b)
+    ring16.insert(sub["pos"], stored, sub["motion"])
+    ref16 = oracle.reconstruct(ring16)["image"]
+    hole = ref16[:, 3] == 0
+    acc = _rel(img[~hole], ref16[~hole, :3])
+    print(f"{ct}: against the FP32 source colours max per channel {mx}, rms per channel {rms}; against the "
+          f"stored colours max rel {acc.max():.3g}")
     assert np.all(rms < 2e-3)
     if max_tol is not None:
-        assert np.quantile(err, 0.999) < max_tol
+        assert err.max() <= max_tol, err.max()
+        assert acc.max() <= 1e-5, acc.max()
+
+
+def _rel(got, want, floor=1e-3):
+    return np.abs(got - want) / np.maximum(np.abs(want), floor)
 
 
 # ----------------------------------------------------------------------------- full size
@@ -216,9 +231,17 @@ def test_full_size_sampled_parity(dev):
     assert np.array_equal(frec[:, :2], wrec[:, :2])
     grads = oracle.gradients(ring, T_NOW)
     wt = oracle.tile_feedback(ring, grads)
+    # every tile holds about 16,000 samples here, so every tile's moments take
+    # the FP64 merge: all AfrTileStats fields against the oracle
     assert np.array_equal(tiles["n"], wt[:, 0].astype(np.uint32))
+    assert np.array_equal(tiles["empty_slots"], wt[:, 1].astype(np.uint32))
+    np.testing.assert_allclose(tiles["mean_L"], wt[:, 2], rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(tiles["var_L"], wt[:, 3], rtol=1e-4, atol=1e-6)
+    for k, f in ((4, "mean_Gx"), (5, "mean_Gy"), (6, "mean_Gt")):
+        np.testing.assert_allclose(tiles[f], wt[:, k], rtol=1e-4, atol=2e-6)
+    np.testing.assert_allclose(tiles["u"], wt[:, 7], rtol=1e-6, atol=1e-6)
     rng = np.random.default_rng(0)
-    pix = rng.choice(W * H, 4096, replace=False)
+    pix = rng.choice(W * H, 16384, replace=False)
     # widths from the oracle's gradients, imported, then the filter at the samples
     L32 = [g.astype(np.float32) for g in grads]
     for m, v in ((L.AFR_MAP_GX, L32[1]), (L.AFR_MAP_GY, L32[2]), (L.AFR_MAP_GT, L32[3])):
@@ -236,10 +259,14 @@ def test_full_size_sampled_parity(dev):
     assert np.all(got[hole] == 0)
     err = np.abs(got[~hole, :3] - ref[~hole, :3]) / np.maximum(np.abs(ref[~hole, :3]), 1e-3)
     assert err.max() <= 1e-5, err.max()
-    # end to end (the benchmark's own widths): the looser end-to-end bound
+    # end to end: the GPU's own gradients, widths and filter, as the benchmark runs them
     full = oracle.reconstruct(ring, pixels=pix)["image"][pix]
-    e2e = np.abs(img[pix, :3] - full[:, :3]) / np.maximum(np.abs(full[:, :3]), 1e-3)
-    assert np.quantile(e2e, 0.99) < 1e-4, np.quantile(e2e, 0.99)
+    hole = full[:, 3] == 0
+    assert np.all(img[pix][hole] == 0)
+    e2e = np.abs(img[pix][~hole, :3] - full[~hole, :3]) / np.maximum(np.abs(full[~hole, :3]), 1e-3)
+    print(f"1920x1080x16 end to end at {pix.size} pixels: max rel err {e2e.max():.3g}, "
+          f"p99.9 {np.quantile(e2e, 0.999):.3g}, {int((e2e > 1e-5).sum())} channel values above 1e-5")
+    assert e2e.max() <= 1e-5, e2e.max()
     # tile error and gain control (sections 6.1, 4.1) over all 2040 tiles
     E, gain = rec.tile_error(0.35, 0.4, 1.25)
     E_ref, g_ref = oracle.tile_error(ring, wt, 32, T_NOW, None, 0.35, 0.4, 1.25)

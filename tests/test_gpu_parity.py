@@ -5,8 +5,10 @@ bit for bit. Floating point follows FP32-vs-FP64 tolerances per stage; each
 stage is checked on the oracle's own input to that stage (imported through
 the ABI) so that the tolerance measures that stage's arithmetic alone:
 
-* gradients:  |d| <= 1e-5 |ref| + 2e-6 (luminance scale ~1: the spatial
-              gradients are differences of means, so they get an absolute floor)
+* gradients:  |d| <= 1e-5 |ref| + 2e-8 (the luminances and their weighted
+              means are double-float; the age weights are FP32, whose relative
+              error ~1e-7 times the spread of a pixel's luminances bounds the
+              absolute error of the spatial gradients, a difference of means)
 * widths:     relative 1e-5
 * filter:     relative 1e-5 per channel with denominator max(|ref|, 1e-3)
 """
@@ -89,7 +91,7 @@ def _grad_close(got, want):
     assert ok.all()
     m = ~np.isnan(want)
     err = np.abs(got[m] - want[m])
-    bound = 1e-5 * np.abs(want[m]) + 2e-6
+    bound = 1e-5 * np.abs(want[m]) + 2e-8
     assert (err <= bound).all(), f"max excess {np.max(err - bound):.3g}"
 
 
@@ -115,6 +117,29 @@ def test_ingest_bitexact(dev, W, H, b, n, batches):
     info = rec.query()
     assert info["rejected"] == ring.rejected and info["resident"] == ring.resident
     assert info["inserted"] == ring.total
+
+
+@pytest.mark.parametrize("W,H,b,dense,spread,batches", [(16, 8, 4, 0, 10000, 2), (40, 20, 8, 8000, 3000, 2),
+                                                        (37, 19, 32, 0, 60000, 1)])
+def test_ingest_dense_cells_bitexact(dev, W, H, b, dense, spread, batches):
+    """Batches denser than one commit round of a 16 x 8 cell (more than 3072
+    records in a cell: rounds over groups of pixels) and a single pixel with
+    more than a round on its own (ranked by a warp streaming the bucket), over
+    consecutive batches, bit for bit against the oracle's queues."""
+    rng = np.random.default_rng(W + H + b)
+    rec = _mk(dev, W, H, b)
+    ring = oracle.Ring(W, H, b)
+    for k in range(batches):
+        batch = _random_batch(rng, dense + spread, W, H, bad=0.02)
+        if dense:
+            idx = rng.permutation(dense + spread)[:dense]
+            batch["pos"][idx, 0] = 3.0 + rng.uniform(0, 0.99, dense).astype(np.float32)
+            batch["pos"][idx, 1] = 2.5
+        _upload(rec, batch)
+        ring.insert(batch["pos"], batch["color"], batch["motion"])
+    _ring_equal(rec, ring)
+    info = rec.query()
+    assert info["rejected"] == ring.rejected and info["resident"] == ring.resident
 
 
 def test_ingest_scene_stream(dev):
@@ -223,10 +248,8 @@ def test_widths_match_oracle(dev, W, H, b):
     np.testing.assert_allclose(rec.export_map(L.AFR_MAP_SIGMA_T), st, rtol=1e-5)
 
 
-def _filter_stage(dev, W, H, b, R=4, speed=24.0, t_shift=0.0, seed=1):
+def _filter_stage(dev, W, H, b, R=4, speed=24.0, seed=1):
     _, _, rec, ring = _setup_scene(dev, W, H, b, R=R, speed=speed, seed=seed)
-    if t_shift:
-        raise NotImplementedError
     rec.estimate_gradients(T_NOW)
     rec.reproject(T_NOW)
     grads = oracle.gradients(ring, T_NOW)
@@ -243,7 +266,10 @@ def _filter_stage(dev, W, H, b, R=4, speed=24.0, t_shift=0.0, seed=1):
 def _check_filter(img, ref, tol=1e-5):
     hole = ref[:, 3] == 0
     np.testing.assert_array_equal(img[hole], 0.0)
-    assert (img[~hole, 3] > 0).all() or True
+    # W is reported as S 2^-m in FP32: nonzero wherever the exact W is within
+    # FP32's normal range (a pixel whose samples are all far older than its
+    # temporal width may report W = 0 and still have exact colours)
+    assert (img[ref[:, 3] > 1e-30, 3] > 0).all()
     err = _rel_err(img[~hole, :3], ref[~hole, :3])
     assert err.max() <= tol, f"max rel err {err.max():.3g} (p99.9 {np.quantile(err, 0.999):.3g})"
     big = ref[:, 3] > 1e-30
@@ -382,11 +408,14 @@ def test_pipelined_steps_match_serial(dev):
 
 
 # ----------------------------------------------------------------------------- end to end
-@pytest.mark.parametrize("key", ["c1_128x128x4"])
-def test_end_to_end_c1(dev, key):
-    """Whole forward path on the static 128x128x4 scene. FP32 gradients feed
-    the widths here, so colours are compared with the end-to-end bound
-    (p99.9 of the relative error below 1e-4, max below 1e-2)."""
+@pytest.mark.parametrize("key", ["c1_128x128x4", "c4_512x512x8", "c2_1024x1024x8"])
+def test_end_to_end_matches_oracle(dev, key):
+    """The whole forward path from the same samples (the GPU's own gradients,
+    widths and filter) against the FP64 oracle's whole path: every colour
+    within 1e-5 relative (denominator max(|ref|, 1e-3)), on the static
+    128x128x4 scene, the moving 512x512x8 scene and the moving, importance-
+    sampled 1024x1024x8 scene. Prints the largest error and the number of
+    channel values above 1e-5."""
     sc, batch = _scene_batch(key)
     W, H, b = sc.width, sc.height, sc.spec.depth
     rec = _mk(dev, W, H, b)
@@ -400,7 +429,11 @@ def test_end_to_end_c1(dev, key):
     hole = ref[:, 3] == 0
     np.testing.assert_array_equal(img[hole], 0.0)
     err = _rel_err(img[~hole, :3], ref[~hole, :3])
-    assert np.quantile(err, 0.999) < 1e-4 and err.max() < 1e-2
+    print(f"{key}: end-to-end max rel err {err.max():.3g}, p99.9 {np.quantile(err, 0.999):.3g}, "
+          f"{int((err > 1e-5).sum())} of {err.size} channel values above 1e-5")
+    assert err.max() <= 1e-5
+    big = ref[:, 3] > 1e-30
+    np.testing.assert_allclose(img[big, 3], ref[big, 3], rtol=1e-4)
 
 
 # ----------------------------------------------------------------------------- adjoint
