@@ -17,8 +17,9 @@
  *    internal buffers and frees them in afr_destroy.
  *  - Compute calls are asynchronous on the given stream and return argument
  *    or call-order errors synchronously. Failures detected on the device
- *    (a bounded wait that ran out, a failed internal check) are recorded in a
- *    device status word that afr_get_status reads (it synchronises).
+ *    (a failed internal check of a debug build, see afr_debug.h) are recorded
+ *    in a device status word that afr_get_status reads (it synchronises the
+ *    stream it is given).
  *  - Nothing throws across the ABI and there is no CPU fallback: when no
  *    CUDA device is usable, afr_create returns AFR_ERR_CUDA.
  *  - Calls on one context are not thread-safe; distinct contexts are
@@ -247,9 +248,13 @@ AFR_API AfrStatus afr_reconstruct_backward(AfrContext *ctx, const float *grad_rg
                                    float *grad_colors_dev, float *grad_params_dev,
                                    afr_stream_t stream);
 
-/* Synchronises the device and returns the first error recorded on it since
- * the last call (and clears it), or AFR_OK. */
-AFR_API AfrStatus afr_get_status(AfrContext *ctx);
+/* Waits for the work issued on stream, then returns the condition recorded in
+ * the context's device status word since the last call (and clears it):
+ * AFR_ERR_DEVICE_CHECK for a failed device-side check (debug builds), or
+ * AFR_OK. Work of this context on other streams is seen once it has
+ * finished (join those streams into this one first). Only this stream is
+ * synchronised, not the device. */
+AFR_API AfrStatus afr_get_status(AfrContext *ctx, afr_stream_t stream);
 
 /* Text of the most recent error on this context ("" if none). The pointer
  * stays valid until the next call on the context. */
@@ -336,6 +341,15 @@ AFR_API AfrStatus afr_set_tuning(AfrContext *ctx, int32_t radius, int32_t tile_b
  * AFR_ERR_BAD_STATE if a stream was being captured into a CUDA graph when a
  * pair would have been recorded (such a launch is not recorded). */
 enum { AFR_PROFILE_MAX_LAUNCHES = 256 };
+
+/* Measured FP32 issue rates of the current device, the denominators of the
+ * filter's roofline (instrumentation; the paper has no counterpart): every
+ * thread of a grid that fills the GPU runs independent chains of one
+ * operation. out_host (4 floats, host memory) receives the scalar FMA rate
+ * and the paired FMA (fma.rn.f32x2) rate in TFLOP/s (2 and 4 FLOP an
+ * instruction), the ex2.approx rate in Tops/s, and the SM count.
+ * Synchronises the device; AFR_ERR_CUDA if a kernel fails. */
+AFR_API AfrStatus afr_measure_alu_peaks(float *out_host);
 AFR_API AfrStatus afr_profile_filter(AfrContext *ctx, int32_t enable);
 AFR_API AfrStatus afr_profile_read(AfrContext *ctx, float *ms_host, int32_t cap, int32_t *count);
 

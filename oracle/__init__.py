@@ -56,8 +56,11 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_SO) >= max(os.path.getmtime(src), os.path.getmtime(hdr))):
         return _SO
     tmp = _SO + f".{os.getpid()}.tmp"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                           "-fno-fast-math", "-o", tmp, src, "-lm"])
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-o", tmp, src, "-lm"]
+    try:   # OpenMP over independent pixels, rows and tiles; results do not depend on it
+        subprocess.check_call(cmd[:-1] + ["-fopenmp", "-lm"], stderr=subprocess.DEVNULL)
+    except subprocess.CalledProcessError:
+        subprocess.check_call(cmd)
     os.replace(tmp, _SO)
     return _SO
 
@@ -71,6 +74,10 @@ def lib():
             P = ctypes.c_void_p
             i64, i32, u32, f32, f64 = (ctypes.c_int64, ctypes.c_int, ctypes.c_uint32,
                                        ctypes.c_float, ctypes.c_double)
+            L.afo_set_threads.restype = None
+            L.afo_set_threads.argtypes = [i32]
+            L.afo_max_threads.restype = i32
+            L.afo_max_threads.argtypes = []
             L.afo_ingest.restype = i64
             L.afo_ingest.argtypes = [i32, i32, i32, P, P, P, u32, i64, P, P, P]
             L.afo_gradients.restype = None
@@ -104,6 +111,15 @@ def lib():
                                        P, P, f32, P, P, P]
             _lib = L
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's loops over independent pixels, rows and tiles."""
+    lib().afo_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(lib().afo_max_threads())
 
 
 def _p(a: np.ndarray):

@@ -12,6 +12,48 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads for the loops over independent pixels, rows and tiles. Each
+ * pixel's (tile's, bin's) computation and every floating-point sum keep
+ * their order, so results do not depend on the thread count. */
+void afo_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int afo_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+static int thread_count(void)
+{
+#ifdef _OPENMP
+    return omp_get_num_threads();
+#else
+    return 1;
+#endif
+}
+
+static int thread_index(void)
+{
+#ifdef _OPENMP
+    return omp_get_thread_num();
+#else
+    return 0;
+#endif
+}
 
 /* Luminance of an RGB colour. The paper measures colour change as luminance
  * change (sections 4, 4.1) without naming the weights; Rec. 709 weights are
@@ -43,35 +85,44 @@ int64_t afo_ingest(int W, int H, int b, int32_t *count, float *slot, uint32_t *s
                    const float *mo)
 {
     int64_t rejected = 0;
-    for (int64_t i = 0; i < n; ++i) {
-        const float *ps = pos + 4 * i, *cs = col + 4 * i, *ms = mo + 2 * i;
-        float x = ps[0], y = ps[1], t = ps[2];
-        int ok = isfinite(x) && isfinite(y) && isfinite(t) && isfinite(cs[0]) &&
-                 isfinite(cs[1]) && isfinite(cs[2]) && isfinite(ms[0]) && isfinite(ms[1]);
-        if (!ok || x < 0.0f || y < 0.0f || x >= (float)W || y >= (float)H) {
-            ++rejected;
-            continue;
+    /* Every pixel's queue is independent of the others, so each thread takes
+     * a band of rows and pushes, in input order, the samples that fall in it. */
+#pragma omp parallel reduction(+ : rejected)
+    {
+        const int nt = thread_count(), me = thread_index();
+        const int y0 = (int)((int64_t)H * me / nt), y1 = (int)((int64_t)H * (me + 1) / nt);
+        for (int64_t i = 0; i < n; ++i) {
+            const float *ps = pos + 4 * i, *cs = col + 4 * i, *ms = mo + 2 * i;
+            float x = ps[0], y = ps[1], t = ps[2];
+            int ok = isfinite(x) && isfinite(y) && isfinite(t) && isfinite(cs[0]) &&
+                     isfinite(cs[1]) && isfinite(cs[2]) && isfinite(ms[0]) && isfinite(ms[1]);
+            if (!ok || x < 0.0f || y < 0.0f || x >= (float)W || y >= (float)H) {
+                if (me == 0) ++rejected;
+                continue;
+            }
+            int row = (int)floorf(y);
+            if (row < y0 || row >= y1) continue;
+            size_t p = (size_t)row * (size_t)W + (size_t)(int)floorf(x);
+            int c = count[p];
+            int last = c < b ? c : b - 1;
+            for (int k = last; k > 0; --k) {
+                memcpy(slot + ((size_t)p * b + k) * AFO_NF, slot + ((size_t)p * b + k - 1) * AFO_NF,
+                       AFO_NF * sizeof(float));
+                seq[(size_t)p * b + k] = seq[(size_t)p * b + k - 1];
+            }
+            float *s = slot + (size_t)p * b * AFO_NF;
+            s[AFO_X] = x;
+            s[AFO_Y] = y;
+            s[AFO_T] = t;
+            s[AFO_DEPTH] = ps[3];
+            s[AFO_R] = cs[0];
+            s[AFO_G] = cs[1];
+            s[AFO_B] = cs[2];
+            s[AFO_MX] = ms[0];
+            s[AFO_MY] = ms[1];
+            seq[(size_t)p * b] = seq0 + (uint32_t)i;
+            if (c < b) count[p] = c + 1;
         }
-        size_t p = (size_t)(int)floorf(y) * (size_t)W + (size_t)(int)floorf(x);
-        int c = count[p];
-        int last = c < b ? c : b - 1;
-        for (int k = last; k > 0; --k) {
-            memcpy(slot + ((size_t)p * b + k) * AFO_NF, slot + ((size_t)p * b + k - 1) * AFO_NF,
-                   AFO_NF * sizeof(float));
-            seq[(size_t)p * b + k] = seq[(size_t)p * b + k - 1];
-        }
-        float *s = slot + (size_t)p * b * AFO_NF;
-        s[AFO_X] = x;
-        s[AFO_Y] = y;
-        s[AFO_T] = t;
-        s[AFO_DEPTH] = ps[3];
-        s[AFO_R] = cs[0];
-        s[AFO_G] = cs[1];
-        s[AFO_B] = cs[2];
-        s[AFO_MX] = ms[0];
-        s[AFO_MY] = ms[1];
-        seq[(size_t)p * b] = seq0 + (uint32_t)i;
-        if (c < b) count[p] = c + 1;
     }
     return rejected;
 }
@@ -124,9 +175,12 @@ void afo_gradients(int W, int H, int b, const int32_t *count, const float *slot,
                    const uint32_t *seq, float t_now, double *Lbar, double *Gx,
                    double *Gy, double *Gt)
 {
+    const int64_t P = (int64_t)W * H;
+#pragma omp parallel
+    {
     int *order = (int *)malloc(sizeof(int) * (size_t)(b > 0 ? b : 1));
-    size_t P = (size_t)W * H;
-    for (size_t p = 0; p < P; ++p) {
+#pragma omp for schedule(static)
+    for (int64_t p = 0; p < P; ++p) {
         int n = count[p];
         if (n == 0) {
             Lbar[p] = NAN;
@@ -170,7 +224,9 @@ void afo_gradients(int W, int H, int b, const int32_t *count, const float *slot,
         Gt[p] = (n >= 2 && den > 0.0) ? num / den : 0.0;
     }
     free(order);
+    }
 
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < H; ++y) {
         for (int x = 0; x < W; ++x) {
             size_t p = (size_t)y * W + x;
@@ -205,6 +261,7 @@ void afo_tile_feedback(int W, int H, int b, int S, const int32_t *count,
 {
     int ntx = (W + S - 1) / S, nty = (H + S - 1) / S;
     double empty_sum = 0.0;
+#pragma omp parallel for collapse(2) schedule(static)
     for (int ty = 0; ty < nty; ++ty) {
         for (int tx = 0; tx < ntx; ++tx) {
             int x0 = tx * S, y0 = ty * S;
@@ -247,9 +304,9 @@ void afo_tile_feedback(int W, int H, int b, int S, const int32_t *count,
             o[AFO_TGX] = nonempty > 0.0 ? gx / nonempty : 0.0;
             o[AFO_TGY] = nonempty > 0.0 ? gy / nonempty : 0.0;
             o[AFO_TGT] = nonempty > 0.0 ? gt / nonempty : 0.0;
-            empty_sum += o[AFO_TEMPTY];
         }
     }
+    for (int i = 0; i < ntx * nty; ++i) empty_sum += out[(size_t)i * AFO_NT + AFO_TEMPTY];
     double mean_empty = empty_sum / ((double)ntx * nty);
     for (int i = 0; i < ntx * nty; ++i) {
         double *o = out + (size_t)i * AFO_NT;
@@ -280,48 +337,83 @@ int64_t afo_reproject(int W, int H, int b, const int32_t *count, const float *sl
                       const uint32_t *seq, float t_now, uint32_t *off, float *rec,
                       uint32_t *rseq, int64_t cap, int64_t *dropped)
 {
-    size_t P = (size_t)W * H, total = 0;
-    for (size_t p = 0; p < P; ++p) total += (size_t)count[p];
-    ReprojEntry *e = (ReprojEntry *)malloc(sizeof(ReprojEntry) * (total ? total : 1));
-    size_t n = 0;
+    size_t P = (size_t)W * H;
+    int nbands = afo_max_threads();
+    if (nbands > H) nbands = H;
+    if (nbands < 1) nbands = 1;
+    ReprojEntry **band = (ReprojEntry **)calloc((size_t)nbands, sizeof(ReprojEntry *));
+    size_t *bn = (size_t *)calloc((size_t)nbands, sizeof(size_t));
     int64_t drop = 0;
-    for (size_t p = 0; p < P; ++p) {
-        for (int k = 0; k < count[p]; ++k) {
-            const float *s = sample_at(slot, b, p, k);
-            float a = t_now - s[AFO_T];
-            float dx = s[AFO_MX] * a;
-            float dy = s[AFO_MY] * a;
-            float xp = s[AFO_X] + dx;
-            float yp = s[AFO_Y] + dy;
-            if (!(xp >= 0.0f && xp < (float)W && yp >= 0.0f && yp < (float)H)) {
-                ++drop;
-                continue;
+    /* Band k collects the samples whose destination row lies in its rows and
+     * sorts them by (bin, sequence number); bins are row-major, so the bands
+     * in order are the whole frame view in that order. */
+#pragma omp parallel for schedule(static, 1) reduction(+ : drop)
+    for (int k = 0; k < nbands; ++k) {
+        const int y0 = (int)((int64_t)H * k / nbands), y1 = (int)((int64_t)H * (k + 1) / nbands);
+        ReprojEntry *e = NULL;
+        size_t n = 0;
+        for (int pass = 0; pass < 2; ++pass) {   /* count the band's samples, then store them */
+            if (pass == 1) {
+                e = (ReprojEntry *)malloc(sizeof(ReprojEntry) * (n ? n : 1));
+                n = 0;
             }
-            e[n].bin = (uint32_t)((int)floorf(yp) * W + (int)floorf(xp));
-            e[n].seq = seq[p * b + k];
-            e[n].v[AFO_RX] = xp;
-            e[n].v[AFO_RY] = yp;
-            e[n].v[AFO_RT] = s[AFO_T];
-            e[n].v[AFO_RR] = s[AFO_R];
-            e[n].v[AFO_RG] = s[AFO_G];
-            e[n].v[AFO_RB] = s[AFO_B];
-            ++n;
+        for (size_t p = 0; p < P; ++p) {
+            for (int j = 0; j < count[p]; ++j) {
+                const float *s = sample_at(slot, b, p, j);
+                float a = t_now - s[AFO_T];
+                float dx = s[AFO_MX] * a;
+                float dy = s[AFO_MY] * a;
+                float xp = s[AFO_X] + dx;
+                float yp = s[AFO_Y] + dy;
+                if (!(xp >= 0.0f && xp < (float)W && yp >= 0.0f && yp < (float)H)) {
+                    if (k == 0 && pass == 1) ++drop;
+                    continue;
+                }
+                int row = (int)floorf(yp);
+                if (row < y0 || row >= y1) continue;
+                if (pass == 0) {
+                    ++n;
+                    continue;
+                }
+                e[n].bin = (uint32_t)(row * W + (int)floorf(xp));
+                e[n].seq = seq[p * b + j];
+                e[n].v[AFO_RX] = xp;
+                e[n].v[AFO_RY] = yp;
+                e[n].v[AFO_RT] = s[AFO_T];
+                e[n].v[AFO_RR] = s[AFO_R];
+                e[n].v[AFO_RG] = s[AFO_G];
+                e[n].v[AFO_RB] = s[AFO_B];
+                ++n;
+            }
         }
+        }
+        qsort(e, n, sizeof(ReprojEntry), entry_cmp);
+        band[k] = e;
+        bn[k] = n;
     }
+    size_t n = 0;
+    for (int k = 0; k < nbands; ++k) n += bn[k];
     if (dropped) *dropped = drop;
     if ((int64_t)n > cap) {
-        free(e);
+        for (int k = 0; k < nbands; ++k) free(band[k]);
+        free(band);
+        free(bn);
         return -1;
     }
-    qsort(e, n, sizeof(ReprojEntry), entry_cmp);
     for (size_t q = 0; q <= P; ++q) off[q] = 0;
-    for (size_t i = 0; i < n; ++i) off[e[i].bin + 1] += 1;
-    for (size_t q = 0; q < P; ++q) off[q + 1] += off[q];
-    for (size_t i = 0; i < n; ++i) {
-        memcpy(rec + i * AFO_NR, e[i].v, sizeof(float) * AFO_NR);
-        rseq[i] = e[i].seq;
+    size_t i = 0;
+    for (int k = 0; k < nbands; ++k) {
+        for (size_t j = 0; j < bn[k]; ++j, ++i) {
+            const ReprojEntry *e = band[k] + j;
+            off[e->bin + 1] += 1;
+            memcpy(rec + i * AFO_NR, e->v, sizeof(float) * AFO_NR);
+            rseq[i] = e->seq;
+        }
+        free(band[k]);
     }
-    free(e);
+    for (size_t q = 0; q < P; ++q) off[q + 1] += off[q];
+    free(band);
+    free(bn);
     return (int64_t)n;
 }
 
@@ -458,6 +550,7 @@ void afo_sigma(int W, int H, int b, int S, const int32_t *count, const double *G
     double *nt = (double *)malloc(sizeof(double) * ntiles);
     double *at = (double *)malloc(sizeof(double) * ntiles);
     tile_counts(W, H, S, count, nt, at);
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) {
             size_t p = (size_t)y * W + x;
@@ -511,6 +604,7 @@ void afo_filter(int W, int H, int R, const uint32_t *off, const float *rec,
                 const int64_t *pixels, int64_t n_pixels, double *out)
 {
     if (pixels) {
+#pragma omp parallel for schedule(dynamic, 256)
         for (int64_t k = 0; k < n_pixels; ++k) {
             int64_t p = pixels[k];
             filter_pixel(W, H, R, off, rec, t_now, sig_s[p], sig_t[p], (int)(p % W),
@@ -518,6 +612,7 @@ void afo_filter(int W, int H, int R, const uint32_t *off, const float *rec,
         }
         return;
     }
+#pragma omp parallel for schedule(dynamic, 4)
     for (int j = 0; j < H; ++j)
         for (int i = 0; i < W; ++i) {
             size_t p = (size_t)j * W + i;

@@ -24,6 +24,11 @@
 extern "C" {
 #endif
 
+/* Threads of the loops over independent pixels, rows and tiles (OpenMP
+ * builds; results do not depend on the count). */
+void afo_set_threads(int n);
+int afo_max_threads(void);
+
 enum { AFO_X = 0, AFO_Y, AFO_T, AFO_DEPTH, AFO_R, AFO_G, AFO_B, AFO_MX, AFO_MY, AFO_NF };
 /* reprojected (frame-view) record: x', y', t, r, g, b */
 enum { AFO_RX = 0, AFO_RY, AFO_RT, AFO_RR, AFO_RG, AFO_RB, AFO_NR };

@@ -11,6 +11,7 @@ import threading
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libafr.so")
+DEBUG_LIB_PATH = os.path.join(_PKG, "libafr_debug.so")   # AFR_DEBUG build: device checks and test hooks
 
 c_i32, c_u32, c_u64, c_f32, c_p = ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_float, ctypes.c_void_p
 
@@ -29,7 +30,7 @@ EXPORTED = [
     "afr_get_status", "afr_last_error", "afr_query", "afr_num_tiles", "afr_export_ring", "afr_export_frame",
     "afr_export_map", "afr_import_map", "afr_set_frame_colors", "afr_reproject_batch_static", "afr_set_tuning",
     "afr_profile_filter", "afr_profile_read", "afr_tile_error", "afr_reproject_camera",
-    "afr_batch_create", "afr_batch_destroy", "afr_batch_reconstruct",
+    "afr_batch_create", "afr_batch_destroy", "afr_batch_reconstruct", "afr_measure_alu_peaks",
 ]
 
 
@@ -60,6 +61,8 @@ class AfrInfo(ctypes.Structure):
 
 _lock = threading.Lock()
 _lib = None
+_debug_lib = None
+DEBUG_EXPORTED = ["afr_debug_fail_alloc", "afr_debug_set_frame_offsets"]
 
 
 def _declare(L):
@@ -76,7 +79,7 @@ def _declare(L):
         "afr_reconstruct_ex": (S, [c_p, c_f32, ctypes.POINTER(AfrParams), c_u32, c_p, c_p]),
         "afr_tile_feedback": (S, [c_p, c_p, c_p]),
         "afr_reconstruct_backward": (S, [c_p, c_p, c_p, c_p, c_p]),
-        "afr_get_status": (S, [c_p]),
+        "afr_get_status": (S, [c_p, c_p]),
         "afr_last_error": (ctypes.c_char_p, [c_p]),
         "afr_query": (S, [c_p, ctypes.POINTER(AfrInfo), c_p]),
         "afr_num_tiles": (S, [c_p, ctypes.POINTER(c_u32)]),
@@ -95,6 +98,7 @@ def _declare(L):
         "afr_batch_create": (S, [ctypes.POINTER(c_p), c_i32, ctypes.POINTER(c_p)]),
         "afr_batch_destroy": (None, [c_p]),
         "afr_batch_reconstruct": (S, [c_p, c_f32, ctypes.POINTER(AfrParams), ctypes.POINTER(c_p), c_p]),
+        "afr_measure_alu_peaks": (S, [c_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -114,6 +118,24 @@ def load():
             _declare(L)
             _lib = L
     return _lib
+
+
+def load_debug():
+    """Load libafr_debug.so, the AFR_DEBUG build (device-side checks and the
+    test hooks of include/afr_debug.h); the same ABI as libafr.so besides."""
+    global _debug_lib
+    with _lock:
+        if _debug_lib is None:
+            if not os.path.exists(DEBUG_LIB_PATH):
+                raise RuntimeError(f"{DEBUG_LIB_PATH} is missing: build the CUDA library first")
+            L = ctypes.CDLL(DEBUG_LIB_PATH)
+            _declare(L)
+            L.afr_debug_fail_alloc.restype = None
+            L.afr_debug_fail_alloc.argtypes = [c_i32]
+            L.afr_debug_set_frame_offsets.restype = c_i32
+            L.afr_debug_set_frame_offsets.argtypes = [c_p, c_p]
+            _debug_lib = L
+    return _debug_lib
 
 
 class AfrError(RuntimeError):

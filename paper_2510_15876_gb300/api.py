@@ -42,8 +42,11 @@ class Reconstructor:
 
     def __init__(self, width: int, height: int, depth: int, *, tile: int = 32, radius: int = 4,
                  color_type: str = "f32", window: float = 1.0, eps_grad: float = 1e-4,
-                 undersample_m: float = 2.0, fifo_capacity: int = 0, world_points: bool = False, device=None):
-        self.lib = L.load()
+                 undersample_m: float = 2.0, fifo_capacity: int = 0, world_points: bool = False, device=None,
+                 lib=None):
+        """lib: the loaded library to use (default libafr.so; L.load_debug()
+        gives the AFR_DEBUG build)."""
+        self.lib = lib if lib is not None else L.load()
         self.device = torch.device(device if device is not None else "cuda")
         if self.device.type != "cuda":
             raise ValueError("the reconstruction library runs on CUDA devices only")
@@ -232,8 +235,10 @@ class Reconstructor:
         return [buf[k] for k in range(min(n.value, L.AFR_PROFILE_MAX_LAUNCHES))]
 
     # -- inspection ----------------------------------------------------------------
-    def status(self) -> int:
-        return self.lib.afr_get_status(self.h)
+    def status(self, stream=None) -> int:
+        """afr_get_status: waits for the work issued on stream (default: the
+        current stream) and returns the device status word's condition."""
+        return self.lib.afr_get_status(self.h, _stream(stream))
 
     def query(self, stream=None) -> dict:
         info = L.AfrInfo()
@@ -320,6 +325,16 @@ class BatchReconstructor:
             self.close()
         except Exception:
             pass
+
+
+def measure_alu_peaks() -> dict:
+    """Measured FP32 rates of the current device (afr_measure_alu_peaks)."""
+    lib = L.load()
+    out = (ctypes.c_float * 4)()
+    st = lib.afr_measure_alu_peaks(out)
+    if st != L.AFR_OK:
+        raise L.AfrError(st, "afr_measure_alu_peaks failed")
+    return {"fma_tflops": out[0], "fma2_tflops": out[1], "ex2_tops": out[2], "sms": int(out[3])}
 
 
 def set_tuning(rec: Reconstructor, radius: int, tile_bx: int):

@@ -7,11 +7,38 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "afr_internal.cuh"
+#ifdef AFR_DEBUG
+#include "../../include/afr_debug.h"
+#endif
 
 using afr::grid_for;
 
 namespace {
+
+// One NVTX range per ABI call (free when no profiler is attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
+
+#ifdef AFR_DEBUG
+// Allocation-failure injection (afr_debug_fail_alloc): the device allocation
+// with this index and every later one fail as if the device were full.
+int g_fail_after = -1;
+int g_allocs = 0;
+#endif
+
+// Every device allocation of the library goes through here.
+cudaError_t dmalloc(void **p, size_t bytes) {
+    *p = nullptr;
+#ifdef AFR_DEBUG
+    if (g_fail_after >= 0 && g_allocs++ >= g_fail_after) return cudaErrorMemoryAllocation;
+#endif
+    return cudaMalloc(p, bytes ? bytes : 1);
+}
 
 AfrStatus fail(AfrContext *c, AfrStatus st, const char *msg) {
     if (c) c->err = msg;
@@ -27,9 +54,7 @@ AfrStatus cuda_fail(AfrContext *c, cudaError_t e, const char *where) {
 
 template <typename T>
 cudaError_t dalloc(T **p, size_t n) {
-    *p = nullptr;
-    if (n == 0) n = 1;
-    return cudaMalloc(reinterpret_cast<void **>(p), n * sizeof(T));
+    return dmalloc(reinterpret_cast<void **>(p), (n ? n : 1) * sizeof(T));
 }
 
 void free_all(AfrContext *c) {
@@ -125,6 +150,7 @@ struct AfrBatch {
 extern "C" {
 
 AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
+    Range nvtx_range("afr_create");
     if (!cfg || !out) return AFR_ERR_INVALID_ARG;
     *out = nullptr;
     const AfrConfig &g = *cfg;
@@ -168,7 +194,7 @@ AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
     AFR_ALLOC(c->r_t, N);
     AFR_ALLOC(c->r_depth, N);
     AFR_ALLOC(c->r_seq, N);
-    if (e == cudaSuccess) e = cudaMalloc(&c->r_col, N * c->csize);
+    if (e == cudaSuccess) e = dmalloc(&c->r_col, N * c->csize);
     AFR_ALLOC(c->r_state, P);
     c->ncells = ((c->W + 15) / 16) * ((c->H + 7) / 8);
     const size_t nkeys = (size_t)c->ncells * afr::ingest_sub_buckets();
@@ -196,12 +222,12 @@ AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
         AFR_ALLOC(c->q_mo, Q);
         AFR_ALLOC(c->q_t, Q);
         AFR_ALLOC(c->q_seq, Q);
-        if (e == cudaSuccess) e = cudaMalloc(&c->q_col, Q * c->csize);
+        if (e == cudaSuccess) e = dmalloc(&c->q_col, Q * c->csize);
         AFR_ALLOC(c->q_total, 1);
         if (e == cudaSuccess) e = cudaMemset(c->q_total, 0, sizeof(uint32_t));
     }
     AFR_ALLOC(c->fpos, c->frame_cap);
-    if (e == cudaSuccess) e = cudaMalloc(&c->fcol, c->frame_cap * c->csize);
+    if (e == cudaSuccess) e = dmalloc(&c->fcol, c->frame_cap * c->csize);
     AFR_ALLOC(c->fseq, c->frame_cap);
     AFR_ALLOC(c->flist, c->frame_cap);
     AFR_ALLOC(c->scan_tmp, c->scan_tmp_n);
@@ -229,6 +255,7 @@ AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
 }
 
 void afr_destroy(AfrContext *c) {
+    Range nvtx_range("afr_destroy");
     if (!c) return;
     cudaDeviceSynchronize();
     if (c->prof_ev) {
@@ -240,6 +267,7 @@ void afr_destroy(AfrContext *c) {
 }
 
 AfrStatus afr_reset(AfrContext *c, afr_stream_t stream) {
+    Range nvtx_range("afr_reset");
     if (!c) return AFR_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(c->r_state, 0, (size_t)c->P * sizeof(uint32_t), s);
@@ -262,6 +290,7 @@ static void free_batch(AfrContext *c) {
 }
 
 AfrStatus afr_reserve(AfrContext *c, uint32_t n) {
+    Range nvtx_range("afr_reserve");
     if (!c) return AFR_ERR_INVALID_ARG;
     if (n <= c->batch_cap) return AFR_OK;
     cudaError_t e = cudaDeviceSynchronize();
@@ -283,6 +312,7 @@ AfrStatus afr_reserve(AfrContext *c, uint32_t n) {
 }
 
 AfrStatus afr_insert_samples(AfrContext *c, const AfrSampleBatch *batch, uint32_t n, afr_stream_t stream) {
+    Range nvtx_range("afr_insert_samples");
     if (!c) return AFR_ERR_INVALID_ARG;
     if (n == 0) return AFR_OK;
     if (!batch || !batch->pos_dev || !batch->color_dev || !batch->motion_dev)
@@ -305,6 +335,7 @@ AfrStatus afr_insert_samples(AfrContext *c, const AfrSampleBatch *batch, uint32_
 }
 
 AfrStatus afr_estimate_gradients(AfrContext *c, float t_now, afr_stream_t stream) {
+    Range nvtx_range("afr_estimate_gradients");
     if (!c) return AFR_ERR_INVALID_ARG;
     if (!std::isfinite(t_now)) return fail(c, AFR_ERR_INVALID_ARG, "afr_estimate_gradients: t_now not finite");
     cudaError_t e = afr::launch_gradients(c, t_now, reinterpret_cast<cudaStream_t>(stream));
@@ -316,6 +347,7 @@ AfrStatus afr_estimate_gradients(AfrContext *c, float t_now, afr_stream_t stream
 }
 
 AfrStatus afr_reproject_camera(AfrContext *c, float t_now, const float *view_proj, afr_stream_t stream) {
+    Range nvtx_range("afr_reproject_camera");
     if (!c) return AFR_ERR_INVALID_ARG;
     if (!std::isfinite(t_now) || !view_proj)
         return fail(c, AFR_ERR_INVALID_ARG, "afr_reproject_camera: t_now not finite or null matrix");
@@ -337,6 +369,7 @@ AfrStatus afr_reproject_camera(AfrContext *c, float t_now, const float *view_pro
 }
 
 AfrStatus afr_reproject(AfrContext *c, float t_now, afr_stream_t stream) {
+    Range nvtx_range("afr_reproject");
     if (!c) return AFR_ERR_INVALID_ARG;
     if (!std::isfinite(t_now)) return fail(c, AFR_ERR_INVALID_ARG, "afr_reproject: t_now not finite");
     cudaError_t e = afr::launch_reproject(c, t_now, nullptr, reinterpret_cast<cudaStream_t>(stream));
@@ -356,6 +389,7 @@ static bool params_ok(const AfrParams *p) {
 
 AfrStatus afr_reconstruct_ex(AfrContext *c, float t_now, const AfrParams *params, uint32_t flags,
                              float *out_rgbw_dev, afr_stream_t stream) {
+    Range nvtx_range("afr_reconstruct_ex");
     if (!c) return AFR_ERR_INVALID_ARG;
     if (!params || !out_rgbw_dev || !aligned(out_rgbw_dev, 16))
         return fail(c, AFR_ERR_INVALID_ARG, "afr_reconstruct: null or misaligned pointer");
@@ -396,10 +430,12 @@ AfrStatus afr_reconstruct_ex(AfrContext *c, float t_now, const AfrParams *params
 
 AfrStatus afr_reconstruct(AfrContext *c, float t_now, const AfrParams *params, float *out_rgbw_dev,
                           afr_stream_t stream) {
+    Range nvtx_range("afr_reconstruct");
     return afr_reconstruct_ex(c, t_now, params, 0u, out_rgbw_dev, stream);
 }
 
 AfrStatus afr_tile_feedback(AfrContext *c, AfrTileStats *out_dev, afr_stream_t stream) {
+    Range nvtx_range("afr_tile_feedback");
     if (!c) return AFR_ERR_INVALID_ARG;
     if (!out_dev) return fail(c, AFR_ERR_INVALID_ARG, "afr_tile_feedback: null output");
     if (!c->grads_valid) return fail(c, AFR_ERR_BAD_STATE, "afr_tile_feedback: call afr_estimate_gradients first");
@@ -410,6 +446,7 @@ AfrStatus afr_tile_feedback(AfrContext *c, AfrTileStats *out_dev, afr_stream_t s
 
 AfrStatus afr_tile_error(AfrContext *c, float kappa, float lambda, float importance, const uint32_t *occluded_dev,
                          float *error_dev, AfrGain *gain_dev, afr_stream_t stream) {
+    Range nvtx_range("afr_tile_error");
     if (!c) return AFR_ERR_INVALID_ARG;
     if (!error_dev) return fail(c, AFR_ERR_INVALID_ARG, "afr_tile_error: null output");
     if (!(kappa >= 0.f && lambda >= 0.f && kappa + lambda <= 1.f) || !(importance >= 0.f) || !std::isfinite(importance))
@@ -424,6 +461,7 @@ AfrStatus afr_tile_error(AfrContext *c, float kappa, float lambda, float importa
 
 AfrStatus afr_reconstruct_backward(AfrContext *c, const float *grad_rgb_dev, float *grad_colors_dev,
                                    float *grad_params_dev, afr_stream_t stream) {
+    Range nvtx_range("afr_reconstruct_backward");
     if (!c) return AFR_ERR_INVALID_ARG;
     if (!grad_rgb_dev || !aligned(grad_rgb_dev, 16))
         return fail(c, AFR_ERR_INVALID_ARG, "afr_reconstruct_backward: null or misaligned grad_rgb");
@@ -440,15 +478,18 @@ AfrStatus afr_reconstruct_backward(AfrContext *c, const float *grad_rgb_dev, flo
     return AFR_OK;
 }
 
-AfrStatus afr_get_status(AfrContext *c) {
+AfrStatus afr_get_status(AfrContext *c, afr_stream_t stream) {
     if (!c) return AFR_ERR_INVALID_ARG;
-    cudaError_t e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) return cuda_fail(c, e, "afr_get_status");
+    Range r("afr_get_status");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     uint32_t w = 0;
-    e = cudaMemcpy(&w, c->derr, sizeof(w), cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaMemcpyAsync(&w, c->derr, sizeof(w), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(c, e, "afr_get_status");
     if (w) {
-        cudaMemset(c->derr, 0, sizeof(uint32_t));
+        e = cudaMemsetAsync(c->derr, 0, sizeof(uint32_t), s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "afr_get_status");
         if (w & afr::ERR_TIMEOUT) return fail(c, AFR_ERR_TIMEOUT, "a bounded device-side wait ran out");
         return fail(c, AFR_ERR_DEVICE_CHECK, "a device-side check failed");
     }
@@ -458,6 +499,7 @@ AfrStatus afr_get_status(AfrContext *c) {
 const char *afr_last_error(const AfrContext *c) { return c ? c->err.c_str() : "null context"; }
 
 AfrStatus afr_query(AfrContext *c, AfrInfo *info, afr_stream_t stream) {
+    Range nvtx_range("afr_query");
     if (!c || !info) return AFR_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = afr::launch_resident_count(c, s);
@@ -477,12 +519,14 @@ AfrStatus afr_query(AfrContext *c, AfrInfo *info, afr_stream_t stream) {
 }
 
 AfrStatus afr_num_tiles(const AfrContext *c, uint32_t *n) {
+    Range nvtx_range("afr_num_tiles");
     if (!c || !n) return AFR_ERR_INVALID_ARG;
     *n = (uint32_t)c->ntiles;
     return AFR_OK;
 }
 
 AfrStatus afr_export_ring(AfrContext *c, int32_t *count_host, float *slot_host, uint32_t *seq_host) {
+    Range nvtx_range("afr_export_ring");
     if (!c || !count_host || !slot_host || !seq_host) return AFR_ERR_INVALID_ARG;
     size_t P = c->P, N = c->nslots;
     std::vector<uint32_t> state(P), seq(N);
@@ -522,6 +566,7 @@ AfrStatus afr_export_ring(AfrContext *c, int32_t *count_host, float *slot_host, 
 }
 
 AfrStatus afr_export_frame(AfrContext *c, uint32_t *off_host, float *rec_host, uint32_t *seq_host, uint64_t cap) {
+    Range nvtx_range("afr_export_frame");
     if (!c || !off_host || !rec_host || !seq_host) return AFR_ERR_INVALID_ARG;
     if (!c->frame_valid) return fail(c, AFR_ERR_BAD_STATE, "afr_export_frame: no frame view");
     cudaError_t e = cudaDeviceSynchronize();
@@ -548,6 +593,7 @@ AfrStatus afr_export_frame(AfrContext *c, uint32_t *off_host, float *rec_host, u
 }
 
 AfrStatus afr_export_map(AfrContext *c, AfrMap which, float *map_host) {
+    Range nvtx_range("afr_export_map");
     if (!c || !map_host) return AFR_ERR_INVALID_ARG;
     size_t P = c->P;
     cudaError_t e = cudaDeviceSynchronize();
@@ -574,6 +620,7 @@ AfrStatus afr_export_map(AfrContext *c, AfrMap which, float *map_host) {
 }
 
 AfrStatus afr_import_map(AfrContext *c, AfrMap which, const float *map_host) {
+    Range nvtx_range("afr_import_map");
     if (!c || !map_host) return AFR_ERR_INVALID_ARG;
     size_t P = c->P;
     cudaError_t e = cudaDeviceSynchronize();
@@ -598,6 +645,7 @@ AfrStatus afr_import_map(AfrContext *c, AfrMap which, const float *map_host) {
 }
 
 AfrStatus afr_set_frame_colors(AfrContext *c, const float *rgb_dev, afr_stream_t stream) {
+    Range nvtx_range("afr_set_frame_colors");
     if (!c || !rgb_dev) return AFR_ERR_INVALID_ARG;
     if (!c->frame_valid) return fail(c, AFR_ERR_BAD_STATE, "afr_set_frame_colors: no frame view");
     cudaError_t e = afr::launch_set_frame_colors(c, rgb_dev, reinterpret_cast<cudaStream_t>(stream));
@@ -611,6 +659,7 @@ AfrStatus afr_set_frame_colors(AfrContext *c, const float *rgb_dev, afr_stream_t
 extern "C" {
 
 AfrStatus afr_profile_filter(AfrContext *c, int32_t enable) {
+    Range nvtx_range("afr_profile_filter");
     if (!c) return AFR_ERR_INVALID_ARG;
     if (enable && !c->prof_ev) {
         c->prof_ev = new cudaEvent_t[2 * AFR_PROFILE_MAX_LAUNCHES]();
@@ -633,6 +682,7 @@ AfrStatus afr_profile_filter(AfrContext *c, int32_t enable) {
 }
 
 AfrStatus afr_profile_read(AfrContext *c, float *ms, int32_t cap, int32_t *count) {
+    Range nvtx_range("afr_profile_read");
     if (!c || !count || (cap > 0 && !ms) || cap < 0) return AFR_ERR_INVALID_ARG;
     *count = 0;
     const int n = c->prof_n;
@@ -652,6 +702,7 @@ AfrStatus afr_profile_read(AfrContext *c, float *ms, int32_t cap, int32_t *count
 }
 
 AfrStatus afr_set_tuning(AfrContext *c, int32_t radius, int32_t tile_bx) {
+    Range nvtx_range("afr_set_tuning");
     if (!c) return AFR_ERR_INVALID_ARG;
     if (radius < 0 || radius > 8 || !(tile_bx == 2 || tile_bx == 4 || tile_bx == 8 || tile_bx == 16))
         return fail(c, AFR_ERR_INVALID_ARG, "afr_set_tuning: radius 0..8, tile_bx 2, 4, 8 or 16");
@@ -663,6 +714,7 @@ AfrStatus afr_set_tuning(AfrContext *c, int32_t radius, int32_t tile_bx) {
 }
 
 void afr_batch_destroy(AfrBatch *b) {
+    Range nvtx_range("afr_batch_destroy");
     if (!b) return;
     cudaDeviceSynchronize();
     if (b->h_ctx) cudaFreeHost(b->h_ctx);
@@ -672,6 +724,7 @@ void afr_batch_destroy(AfrBatch *b) {
 }
 
 AfrStatus afr_batch_create(AfrContext *const *ctxs, int32_t n, AfrBatch **out) {
+    Range nvtx_range("afr_batch_create");
     if (!ctxs || !out || n < 1 || n > 64) return AFR_ERR_INVALID_ARG;
     *out = nullptr;
     for (int i = 0; i < n; ++i)
@@ -688,8 +741,8 @@ AfrStatus afr_batch_create(AfrContext *const *ctxs, int32_t n, AfrBatch **out) {
         b->tile_bx.push_back(ctxs[i]->tile_bx);
     }
     cudaError_t e = cudaMallocHost(&b->h_ctx, sizeof(afr::BatchCtx) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_ctx, sizeof(afr::BatchCtx) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, sizeof(uint32_t));
+    if (e == cudaSuccess) e = dmalloc(reinterpret_cast<void **>(&b->d_ctx), sizeof(afr::BatchCtx) * n);
+    if (e == cudaSuccess) e = dmalloc(reinterpret_cast<void **>(&b->d_queue), sizeof(uint32_t));
     // Contexts larger than afr::kBatchDirectPixels are reconstructed with their
     // own launches inside the batched call: measured on GB300, the persistent
     // kernel is about 30% faster than separate launches for 256x256 streams
@@ -723,6 +776,7 @@ AfrStatus afr_batch_create(AfrContext *const *ctxs, int32_t n, AfrBatch **out) {
 
 AfrStatus afr_batch_reconstruct(AfrBatch *b, float t_now, const AfrParams *params, float *const *outs_dev,
                                 afr_stream_t stream) {
+    Range nvtx_range("afr_batch_reconstruct");
     if (!b || !params || !outs_dev) return AFR_ERR_INVALID_ARG;
     if (!params_ok(params)) return AFR_ERR_INVALID_ARG;
     const int n = (int)b->ctxs.size();
@@ -757,6 +811,7 @@ AfrStatus afr_batch_reconstruct(AfrBatch *b, float t_now, const AfrParams *param
         x.fcol = c->fcol;
         x.out = reinterpret_cast<float4 *>(o);
         x.derr = c->derr;
+        x.fcap = (uint32_t)c->frame_cap;
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // the pinned staging buffer may still feed an earlier copy on the stream:
@@ -797,3 +852,24 @@ AfrStatus afr_batch_reconstruct(AfrBatch *b, float t_now, const AfrParams *param
 }
 
 }  // extern "C"
+
+#ifdef AFR_DEBUG
+extern "C" {
+
+void afr_debug_fail_alloc(int32_t after) {
+    g_fail_after = after;
+    g_allocs = 0;
+}
+
+AfrStatus afr_debug_set_frame_offsets(AfrContext *c, const uint32_t *off_host) {
+    if (!c || !off_host) return AFR_ERR_INVALID_ARG;
+    for (int p = 0; p < c->P; ++p)
+        if (off_host[p + 1] < off_host[p]) return fail(c, AFR_ERR_INVALID_ARG, "offsets must not decrease");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(c->foff, off_host, sizeof(uint32_t) * ((size_t)c->P + 1), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "afr_debug_set_frame_offsets");
+    return AFR_OK;
+}
+
+}  // extern "C"
+#endif

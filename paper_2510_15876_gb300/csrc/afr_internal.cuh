@@ -25,6 +25,26 @@ enum { CNT_REJECTED = 0, CNT_DROPPED, CNT_UNSORTED, CNT_RESIDENT, CNT_BIG, CNT_N
 // device status word bits
 enum { ERR_TIMEOUT = 1u, ERR_CHECK = 2u };
 
+// Device-side consistency checks (builds with AFR_DEBUG): a failed check sets
+// ERR_CHECK in the context's status word, which afr_get_status reports, and
+// the caller skips the access it guarded. Release builds compile the checks
+// out (AFR_CHECK is the constant true and its condition is not evaluated).
+#ifdef AFR_DEBUG
+__device__ __forceinline__ bool dcheck(bool ok, uint32_t *derr) {
+    if (!ok) atomicOr(derr, (uint32_t)ERR_CHECK);
+    return ok;
+}
+#define AFR_CHECK(cond, derr) ::afr::dcheck((cond), (derr))
+#else
+#define AFR_CHECK(cond, derr) true
+#endif
+
+// Bounds of one array for the checks: its element count and the status word.
+struct DebugCheck {
+    uint32_t cap;
+    uint32_t *derr;
+};
+
 // Per-tile partial statistics written by the gradient pass (64 bytes). The
 // luminance moments are FP64 because a tile above 4096 samples merges its
 // warps' moments in FP64; everything else is an integer count or an FP32 sum.
@@ -59,6 +79,7 @@ struct BatchCtx {
     const void *fcol;
     float4 *out;
     uint32_t *derr;
+    uint32_t fcap;      // frame-view record capacity (checks)
     uint32_t a0;        // first work item (tile) of this context
     uint32_t s0;        // first width chunk of this context
 };

@@ -339,7 +339,7 @@ template <int CT, bool KAHAN, bool VAR>
 __device__ __forceinline__ void filter_block(int W, int H, int Rfix, int bx, int by, const float4 *__restrict__ fconst,
                                              const uint32_t *__restrict__ foff, const float4 *__restrict__ fpos,
                                              const void *__restrict__ fcol, float4 *__restrict__ out,
-                                             QuadSmem &sm) {
+                                             QuadSmem &sm, const DebugCheck &dc) {
     using CS = ColorStore<CT>;
     const int lane = threadIdx.x & 31;
     float4 fc = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));   // -1: no pixel
@@ -391,6 +391,7 @@ __device__ __forceinline__ void filter_block(int W, int H, int Rfix, int bx, int
             const size_t q = (size_t)row * W;
             first = __ldg(foff + q + c0);
             cnt = __ldg(foff + q + c1 + 1) - first;
+            if (!AFR_CHECK(__ldg(foff + q + c1 + 1) >= first && cnt <= dc.cap, dc.derr)) cnt = 0;
         }
     }
     const uint32_t incl = warp_incl_scan_u(cnt);
@@ -430,19 +431,35 @@ __device__ __forceinline__ void filter_block(int W, int H, int Rfix, int bx, int
     for (; j + 32 < total; j += 64) {
         advance(ka, j, sm, span, colofs);
         advance(kb, j + 32, sm, span, colofs);
-        const uint32_t ia = j + ka.base, ib = j + 32 + kb.base;
+        uint32_t ia = j + ka.base, ib = j + 32 + kb.base;
+        const bool va = AFR_CHECK(ia < dc.cap, dc.derr), vb = AFR_CHECK(ib < dc.cap, dc.derr);
+        if (!va) ia = 0;   // skipped: record 0 read, weight 0
+        if (!vb) ib = 0;
         const float4 ra = __ldg(fpos + ia), rb = __ldg(fpos + ib);
         const float3 ca = CS::load(fcol, ia), cbv = CS::load(fcol, ib);
-        const float4 sa = sm.shift[ka.tb + __float_as_int(ra.w)];
-        const float4 sb = sm.shift[kb.tb + __float_as_int(rb.w)];
+        int ta = ka.tb + __float_as_int(ra.w), tb = kb.tb + __float_as_int(rb.w);
+        const bool wa = va && AFR_CHECK(ta >= 0 && ta < kMaxRows * kMaxRows, dc.derr);
+        const bool wb = vb && AFR_CHECK(tb >= 0 && tb < kMaxRows * kMaxRows, dc.derr);
+        if (!wa) ta = 0;
+        if (!wb) tb = 0;
+        float4 sa = sm.shift[ta], sb = sm.shift[tb];
+        if (!wa) sa = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+        if (!wb) sb = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
         accumulate<KAHAN>(pc, sa, ra, ca, A);
         accumulate<KAHAN>(pc, sb, rb, cbv, A);
     }
     if (j < total) {
         advance(ka, j, sm, span, colofs);
-        const uint32_t ia = j + ka.base;
+        uint32_t ia = j + ka.base;
+        const bool va = AFR_CHECK(ia < dc.cap, dc.derr);
+        if (!va) ia = 0;
         const float4 ra = __ldg(fpos + ia);
-        accumulate<KAHAN>(pc, sm.shift[ka.tb + __float_as_int(ra.w)], ra, CS::load(fcol, ia), A);
+        int ta = ka.tb + __float_as_int(ra.w);
+        const bool wa = va && AFR_CHECK(ta >= 0 && ta < kMaxRows * kMaxRows, dc.derr);
+        if (!wa) ta = 0;
+        float4 sa = sm.shift[ta];
+        if (!wa) sa = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+        accumulate<KAHAN>(pc, sa, ra, CS::load(fcol, ia), A);
     }
     float vals[16];
 #pragma unroll
@@ -486,14 +503,15 @@ __device__ __forceinline__ void filter_block(int W, int H, int Rfix, int bx, int
 template <int CT, bool KAHAN, bool VAR>
 __global__ void __launch_bounds__(256, 3) k_filter(int W, int H, int R, int tbx, const float4 *__restrict__ fconst,
                                                    const uint32_t *__restrict__ foff, const float4 *__restrict__ fpos,
-                                                   const void *__restrict__ fcol, float4 *__restrict__ out) {
+                                                   const void *__restrict__ fcol, float4 *__restrict__ out,
+                                                   DebugCheck dc) {
     __shared__ QuadSmem smem[kWarps];
     const int warp = threadIdx.x >> 5;
     const int tby = 32 / tbx;
     for (int blk = warp; blk < 32; blk += kWarps) {
         const int bx = blockIdx.x * 2 * tbx + (blk % tbx) * 2, by = blockIdx.y * 2 * tby + (blk / tbx) * 2;
         if (bx >= W || by >= H) continue;   // warp-uniform
-        filter_block<CT, KAHAN, VAR>(W, H, R, bx, by, fconst, foff, fpos, fcol, out, smem[warp]);
+        filter_block<CT, KAHAN, VAR>(W, H, R, bx, by, fconst, foff, fpos, fcol, out, smem[warp], dc);
     }
 }
 
@@ -571,7 +589,7 @@ __global__ void __launch_bounds__(256, 3) k_batch(const BatchCtx *__restrict__ c
             const int bx = tile * tw + (blk % tbx) * 2, by = band * th + (blk / tbx) * 2;
             if (bx >= x.W || by >= x.H) continue;
             filter_block<CT, KAHAN, false>(x.W, x.H, x.R, bx, by, x.fconst, x.foff, x.fpos, x.fcol, x.out,
-                                           smem[warp]);
+                                           smem[warp], DebugCheck{x.fcap, x.derr});
         }
         __syncthreads();
     }
@@ -756,11 +774,12 @@ cudaError_t launch_coverage_init(AfrContext *c, cudaStream_t s) {
 
 cudaError_t launch_filter(AfrContext *c, float t_now, bool adaptive, float4 *out, cudaStream_t s) {
     (void)t_now;
+    const DebugCheck dc{(uint32_t)c->frame_cap, c->derr};
     const int tbx = c->tile_bx, tw = 2 * tbx, th = 2 * (32 / tbx);
     dim3 grid((c->W + tw - 1) / tw, (c->H + th - 1) / th);
 #define AFR_FILTER(CT_, K_, V_)                                                                          \
     k_filter<CT_, K_, V_><<<grid, kQuadBlock, 0, s>>>(c->W, c->H, c->R, tbx, c->fconst, c->foff, c->fpos, c->fcol, \
-                                                      out)
+                                                      out, dc)
     switch (c->ct) {
         case AFR_F32:
             if (adaptive) AFR_FILTER(AFR_F32, false, true);

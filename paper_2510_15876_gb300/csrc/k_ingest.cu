@@ -59,6 +59,7 @@ struct Queues {
     void *col;
     uint32_t *state;   // count | head << 16
     float4 *world;
+    size_t nslots;     // P * b (checks)
 };
 
 __device__ __forceinline__ bool position_ok(float4 p, int W, int H) {
@@ -92,7 +93,8 @@ template <int CT>
 __global__ void __launch_bounds__(32 * kScatterWarps) k_cell_scatter(
     const float4 *__restrict__ pos, const void *__restrict__ col, const float2 *__restrict__ mo,
     const float4 *__restrict__ world, uint32_t n, int W, int H, int ncx, const uint32_t *__restrict__ coff,
-    uint32_t *__restrict__ ccur, Bucket bk, uint32_t *__restrict__ accept, unsigned long long *__restrict__ dcount) {
+    uint32_t *__restrict__ ccur, Bucket bk, uint32_t *__restrict__ accept, unsigned long long *__restrict__ dcount,
+    DebugCheck dc) {
     using CS = ColorStore<CT>;
     __shared__ uint4 stage[kScatterWarps][32][5];   // 80-byte stride: conflict-free 16-byte accesses
     __shared__ uint32_t dest[kScatterWarps][32];
@@ -126,6 +128,7 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_cell_scatter(
             if (pok) {
                 const uint32_t key = cell_of(p[r].x, p[r].y, ncx) * kSubBuckets + (i & (kSubBuckets - 1));
                 d[r] = __ldg(coff + key) + atomicAdd(ccur + key, 1u);
+                if (!AFR_CHECK(d[r] < dc.cap, dc.derr)) d[r] = kInvalid;
             }
         }
 #pragma unroll
@@ -248,9 +251,12 @@ constexpr int kPutUnroll = 2;      // kept records in flight per thread (queue w
 // Writes kept records (bucket position src, queue slot dst, sequence number)
 // field by field, the loads of each field issued together.
 template <int CT>
-__device__ __forceinline__ void put_entries(const Bucket &bk, uint32_t c0, const uint32_t (&src)[kPutUnroll],
+__device__ __forceinline__ void put_entries(const Bucket &bk, uint32_t c0, uint32_t (&src)[kPutUnroll],
                                             const size_t (&dst)[kPutUnroll], const uint32_t (&seq)[kPutUnroll],
-                                            const Queues &q) {
+                                            const Queues &q, const DebugCheck &dc) {
+#pragma unroll
+    for (int r = 0; r < kPutUnroll; ++r)   // dc.cap: bucket records; q.nslots: queue slots
+        if (src[r] != kInvalid && !AFR_CHECK(c0 + src[r] < dc.cap && dst[r] < q.nslots, dc.derr)) src[r] = kInvalid;
     uint4 a[kPutUnroll], q1[kPutUnroll];
 #pragma unroll
     for (int r = 0; r < kPutUnroll; ++r)
@@ -293,7 +299,8 @@ __device__ __forceinline__ void put_entries(const Bucket &bk, uint32_t c0, const
 
 template <int CT>
 __global__ void __launch_bounds__(kCommitThreads, 2) k_cell_commit(const uint32_t *__restrict__ coff, int W, int H,
-                                                                   int ncx, int b, uint32_t seq0, Bucket bk, Queues q) {
+                                                                   int ncx, int b, uint32_t seq0, Bucket bk, Queues q,
+                                                                   DebugCheck dc) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const CommitSmem sm = commit_smem(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -351,7 +358,7 @@ __global__ void __launch_bounds__(kCommitThreads, 2) k_cell_commit(const uint32_
                 seq[0] = seq0 + (uint32_t)(top >> 32) - 1u;
                 dst[0] = pixel_of(l) * ub + ((sm.state[l] >> 16) + rank) % ub;
             }
-            put_entries<CT>(bk, c0, src, dst, seq, q);
+            put_entries<CT>(bk, c0, src, dst, seq, q, dc);
         }
     }
     uint32_t group_begin = 0;
@@ -467,7 +474,7 @@ __global__ void __launch_bounds__(kCommitThreads, 2) k_cell_commit(const uint32_
                 seq[r] = seq0 + me;
                 dst[r] = pixel_of(l) * ub + ((sm.state[l] >> 16) + rank) % ub;
             }
-            put_entries<CT>(bk, c0, src, dst, seq, q);
+            put_entries<CT>(bk, c0, src, dst, seq, q, dc);
         }
         // more than 32: a warp keeps the newest 32 by bitonic merges of the
         // pixel's records, 32 at a time
@@ -495,7 +502,7 @@ __global__ void __launch_bounds__(kCommitThreads, 2) k_cell_commit(const uint32_
                 seq[0] = seq0 + sm.sidx[u];
                 dst[0] = pixel_of(l) * ub + ((sm.state[l] >> 16) + rank) % ub;
             }
-            put_entries<CT>(bk, c0, src, dst, seq, q);
+            put_entries<CT>(bk, c0, src, dst, seq, q, dc);
         }
         __syncthreads();
         group_begin = ge;
@@ -516,6 +523,7 @@ cudaError_t run(AfrContext *c, const float4 *pos, const void *col, const float2 
                 uint32_t seq0, cudaStream_t s) {
     const int ncx = (c->W + kCellW - 1) / kCellW;
     const int nkeys = c->ncells * kSubBuckets;
+    const DebugCheck dc{(uint32_t)c->batch_cap, c->derr};
     Bucket bk{c->bucket, c->r_world != nullptr};
     static bool attr_set = false;   // per colour type: raise the commit kernel's shared-memory limit once
     cudaError_t e = cudaSuccess;
@@ -532,9 +540,10 @@ cudaError_t run(AfrContext *c, const float4 *pos, const void *col, const float2 
     if ((e = scan_exclusive(c->ccnt, c->coff, nkeys, c->scan_tmp, s)) != cudaSuccess) return e;
     const int gs = grid_for((n + kScatterUnroll - 1) / kScatterUnroll, 32 * kScatterWarps);
     k_cell_scatter<CT><<<gs, 32 * kScatterWarps, 0, s>>>(pos, col, mo, world, n, c->W, c->H, ncx, c->coff, c->ccur,
-                                                          bk, c->fifo_n ? c->fifo_flag : nullptr, c->dcount);
-    Queues q{c->r_xy, c->r_mo, c->r_t, c->r_depth, c->r_seq, c->r_col, c->r_state, c->r_world};
-    k_cell_commit<CT><<<c->ncells, kCommitThreads, kCommitSmemBytes, s>>>(c->coff, c->W, c->H, ncx, c->b, seq0, bk, q);
+                                                          bk, c->fifo_n ? c->fifo_flag : nullptr, c->dcount, dc);
+    Queues q{c->r_xy, c->r_mo, c->r_t, c->r_depth, c->r_seq, c->r_col, c->r_state, c->r_world, c->nslots};
+    k_cell_commit<CT><<<c->ncells, kCommitThreads, kCommitSmemBytes, s>>>(c->coff, c->W, c->H, ncx, c->b, seq0, bk, q,
+                                                                          dc);
     return cudaGetLastError();
 }
 

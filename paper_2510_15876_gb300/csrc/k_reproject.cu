@@ -158,12 +158,13 @@ __global__ void __launch_bounds__(256) k_list(uint32_t nslots, int b, int bshift
                                               const uint32_t *__restrict__ state, const float2 *__restrict__ r_xy,
                                               const float2 *__restrict__ r_mo, const float *__restrict__ r_t,
                                               const uint32_t *__restrict__ foff, uint32_t *__restrict__ fcur,
-                                              uint32_t *__restrict__ flist) {
+                                              uint32_t *__restrict__ flist, DebugCheck dc) {
     const uint32_t nlive = FIFO ? min(__ldg(state), nslots) : 0u;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nslots; i += gridDim.x * blockDim.x) {
         Moved mv;
         if (!live_move<FIFO, CAM>(i, nlive, b, bshift, W, H, t_now, cam, world, state, r_xy, r_mo, r_t, mv)) continue;
-        flist[__ldg(foff + mv.bin) + agg_inc(fcur, mv.bin)] = i;
+        const uint32_t at = __ldg(foff + mv.bin) + agg_inc(fcur, mv.bin);
+        if (AFR_CHECK(at < dc.cap, dc.derr)) flist[at] = i;
     }
 }
 
@@ -177,11 +178,13 @@ __global__ void __launch_bounds__(256) k_place(int W, int H, float t_now, Camera
                                                const uint32_t *__restrict__ foff, const uint32_t *__restrict__ flist,
                                                uint32_t *__restrict__ fcnt, float4 *__restrict__ fpos,
                                                void *__restrict__ fcol, uint32_t *__restrict__ fseq,
-                                               unsigned long long *__restrict__ dcount) {
+                                               unsigned long long *__restrict__ dcount, DebugCheck dc, uint32_t nsrc) {
     using CS = ColorStore<CT>;
-    const uint32_t n = __ldg(foff + P);
+    uint32_t n = __ldg(foff + P);
+    if (!AFR_CHECK(n <= dc.cap, dc.derr)) n = 0;
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         const uint32_t i = __ldg(flist + e);
+        if (!AFR_CHECK(i < nsrc, dc.derr)) continue;
         const Moved mv = CAM ? move_camera(__ldg(world + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H, cam)
                              : move_sample(__ldg(r_xy + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H);
         const uint32_t sq = __ldg(r_seq + i);
@@ -194,6 +197,7 @@ __global__ void __launch_bounds__(256) k_place(int W, int H, float t_now, Camera
             if (rank == 0) atomicAdd(dcount + CNT_UNSORTED, 1ull);
         }
         const uint32_t d = beg + rank;
+        if (!AFR_CHECK(d < n, dc.derr)) continue;
         fpos[d] = make_float4(mv.xp, mv.yp, mv.a2, __int_as_float((int)floorf(mv.xp)));
         reinterpret_cast<typename CS::T *>(fcol)[d] = CS::raw(r_col, i);
         fseq[d] = sq;
@@ -225,6 +229,7 @@ cudaError_t launch_reproject(AfrContext *c, float t_now, const Camera *camp, cud
     const int g = grid_for(nsrc, 256);
     const uint32_t ns = (uint32_t)nsrc;
     const int bshift = (c->b & (c->b - 1)) == 0 ? __builtin_ctz((unsigned)c->b) : -1;
+    const DebugCheck dc{(uint32_t)c->frame_cap, c->derr};
 #define AFR_COUNT(F_, C_)                                                                                    \
     k_count<F_, C_><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, cm, wp, state, xy, mo, tt, c->fcnt, \
                                       c->amin2, c->dcount)
@@ -237,7 +242,7 @@ cudaError_t launch_reproject(AfrContext *c, float t_now, const Camera *camp, cud
     if ((e = cudaMemsetAsync(c->fcnt, 0, sizeof(uint32_t) * c->P, s)) != cudaSuccess) return e;
 #define AFR_LIST(F_, C_)                                                                                       \
     k_list<F_, C_><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, cm, wp, state, xy, mo, tt, c->foff,  \
-                                     c->fcnt, c->flist)
+                                     c->fcnt, c->flist, dc)
     if (fifo && cam) AFR_LIST(true, true);
     else if (fifo) AFR_LIST(true, false);
     else if (cam) AFR_LIST(false, true);
@@ -245,7 +250,7 @@ cudaError_t launch_reproject(AfrContext *c, float t_now, const Camera *camp, cud
 #undef AFR_LIST
 #define AFR_PLACE(CT_, F_, C_)                                                                                     \
     k_place<CT_, F_, C_><<<g, 256, 0, s>>>(c->W, c->H, t_now, cm, wp, xy, mo, tt, sq, col, (uint32_t)c->P, c->foff, \
-                                           c->flist, c->fcnt, c->fpos, c->fcol, c->fseq, c->dcount)
+                                           c->flist, c->fcnt, c->fpos, c->fcol, c->fseq, c->dcount, dc, ns)
 #define AFR_REPROJ(CT_)                                                                                        \
     do {                                                                                                       \
         if (fifo && cam) AFR_PLACE(CT_, true, true);                                                           \

@@ -63,3 +63,21 @@ def test_no_device_means_loud_failure(lib):
     from paper_2510_15876_gb300.api import Reconstructor
     with pytest.raises(Exception):
         Reconstructor(8, 8, 4, device="cuda")
+
+
+def _declared_debug():
+    txt = open(os.path.join(ROOT, "include", "afr_debug.h")).read()
+    return sorted(set(re.findall(r"^AFR_API\s+[\w\s\*]*?\b(afr_\w+)\s*\(", txt, flags=re.M)))
+
+
+def test_debug_library_exports_its_hooks(lib):
+    """libafr_debug.so (the AFR_DEBUG build) exports the whole ABI plus the
+    hooks of include/afr_debug.h; the release library has no hook."""
+    from paper_2510_15876_gb300 import _lib
+    dbg = _lib.load_debug()
+    hooks = _declared_debug()
+    assert hooks == sorted(_lib.DEBUG_EXPORTED)
+    for n in _declared() + hooks:
+        assert hasattr(dbg, n), n
+    for n in hooks:
+        assert not hasattr(lib, n), n
