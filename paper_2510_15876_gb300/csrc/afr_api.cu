@@ -60,7 +60,7 @@ cudaError_t dalloc(T **p, size_t n) {
 void free_all(AfrContext *c) {
     void *ptrs[] = {c->r_xy, c->r_mo, c->r_t, c->r_depth, c->r_seq, c->r_col, c->r_state, c->bucket, c->fifo_flag, c->fifo_rank, c->fifo_scan,
                     c->ccnt, c->coff, c->ccur, c->lbar, c->grad, c->pstat, c->sigma, c->tile_terms, c->fconst, c->cov_r[0], c->cov_r[1], c->cov_n, c->amin2, c->tiles, c->fcnt,
-                    c->foff, c->fpos, c->fcol, c->fseq, c->flist, c->q_xy, c->q_mo, c->q_t, c->q_seq, c->q_col, c->q_total, c->q_world, c->r_world, c->scan_tmp, c->bgrad, c->bparam, c->dcount, c->derr};
+                    c->foff, c->fpos, c->fcol, c->fseq, c->flist, c->flseq, c->q_xy, c->q_mo, c->q_t, c->q_seq, c->q_col, c->q_total, c->q_world, c->r_world, c->scan_tmp, c->bgrad, c->bparam, c->dcount, c->derr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -230,6 +230,7 @@ AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
     if (e == cudaSuccess) e = dmalloc(&c->fcol, c->frame_cap * c->csize);
     AFR_ALLOC(c->fseq, c->frame_cap);
     AFR_ALLOC(c->flist, c->frame_cap);
+    AFR_ALLOC(c->flseq, c->frame_cap);
     AFR_ALLOC(c->scan_tmp, c->scan_tmp_n);
     AFR_ALLOC(c->bgrad, 2 * P);
     AFR_ALLOC(c->bparam, (size_t)c->n_bblocks * 6);
@@ -296,7 +297,7 @@ AfrStatus afr_reserve(AfrContext *c, uint32_t n) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(c, e, "afr_reserve");
     free_batch(c);
-    e = dalloc(&c->bucket, 4 * (size_t)n);
+    e = dalloc(&c->bucket, 4 * (size_t)n);   // 64-byte records
     if (c->fifo_n) {
         if (e == cudaSuccess) e = dalloc(&c->fifo_flag, n);
         if (e == cudaSuccess) e = dalloc(&c->fifo_rank, (size_t)n + 1);   // the scan also writes the total

@@ -147,6 +147,7 @@ struct AfrContext {
     void *fcol = nullptr;         // [frame_cap]
     uint32_t *fseq = nullptr;     // [frame_cap] sequence numbers
     uint32_t *flist = nullptr;    // [frame_cap] each bin's source slots, unordered (reprojection scratch)
+    uint32_t *flseq = nullptr;    // [frame_cap] their sequence numbers
     size_t frame_cap = 0;
 
     // scan scratch

@@ -40,15 +40,15 @@ constexpr int kCommitCap = 3072;      // records of one round in shared memory
 constexpr int kCommitThreads = 512;
 constexpr int kCommitWarps = kCommitThreads / 32;
 
-// Bucket records, 64 bytes each as four uint4:
-//   q0 = (x, y, t, depth)
-//   q1 = (batch index, m_y for FP32 colours, hit point X, Y)
-//   q2 = FP32: (r, g, b, m_x); 16-bit: (r | g << 16, b, m_x, m_y)
+// Bucket records, NP = 4 uint4 (64 bytes: two whole sectors) each:
+//   q0 = (x, y, t, batch index)
+//   q1 = FP32: (r, g, b, m_x); 16-bit: (r | g << 16, b, m_x, m_y)
+//   q2 = (m_y for FP32 colours, depth, hit point X, Y)
 //   q3 = (hit point Z, 0, 0, 0)
-// The first sector (q0, q1) is all the commit's sort reads.
+// The first 16 bytes are all the commit's sort reads. (Three-part, 48-byte
+// records, whose halves of a shared sector L2 has to merge, measured slower.)
 struct Bucket {
-    uint4 *r;    // [4 * batch_cap]
-    bool world;  // records carry hit points
+    uint4 *r;    // [NP * batch_cap]
 };
 
 // Destination planes of the queues (slot p * b + s).
@@ -89,7 +89,7 @@ __device__ __forceinline__ bool sample_ok(float4 p, typename ColorStore<CT>::T c
 constexpr int kScatterWarps = 8;
 constexpr int kScatterUnroll = 4;   // samples (and ticket atomics) in flight per thread
 
-template <int CT>
+template <int CT, int NP>
 __global__ void __launch_bounds__(32 * kScatterWarps) k_cell_scatter(
     const float4 *__restrict__ pos, const void *__restrict__ col, const float2 *__restrict__ mo,
     const float4 *__restrict__ world, uint32_t n, int W, int H, int ncx, const uint32_t *__restrict__ coff,
@@ -136,33 +136,34 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_cell_scatter(
             const uint32_t i = base + r * 32 + lane;
             if (d[r] != kInvalid) {
                 float4 wp = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (bk.world && ok[r]) wp = __ldg(world + i);
-                uint4 q2;
+                if (NP == 4 && ok[r] && world) wp = __ldg(world + i);
+                uint4 q1;
                 uint32_t my = 0u;
                 if (CT == AFR_F32) {
                     const float4 cf = *reinterpret_cast<const float4 *>(&cr[r]);
-                    q2 = make_uint4(__float_as_uint(cf.x), __float_as_uint(cf.y), __float_as_uint(cf.z),
+                    q1 = make_uint4(__float_as_uint(cf.x), __float_as_uint(cf.y), __float_as_uint(cf.z),
                                     __float_as_uint(m[r].x));
                     my = __float_as_uint(m[r].y);
                 } else {
                     const ushort4 h = *reinterpret_cast<const ushort4 *>(&cr[r]);
-                    q2 = make_uint4((uint32_t)h.x | ((uint32_t)h.y << 16), (uint32_t)h.z, __float_as_uint(m[r].x),
+                    q1 = make_uint4((uint32_t)h.x | ((uint32_t)h.y << 16), (uint32_t)h.z, __float_as_uint(m[r].x),
                                     __float_as_uint(m[r].y));
                 }
                 stage[w][lane][0] = make_uint4(__float_as_uint(p[r].x), __float_as_uint(p[r].y),
-                                               __float_as_uint(p[r].z), __float_as_uint(p[r].w));
-                stage[w][lane][1] = make_uint4(ok[r] ? i : kInvalid, my, __float_as_uint(wp.x), __float_as_uint(wp.y));
-                stage[w][lane][2] = q2;
-                stage[w][lane][3] = make_uint4(__float_as_uint(wp.z), 0u, 0u, 0u);
+                                               __float_as_uint(p[r].z), ok[r] ? i : kInvalid);
+                stage[w][lane][1] = q1;
+                stage[w][lane][2] = make_uint4(my, __float_as_uint(p[r].w), __float_as_uint(wp.x), __float_as_uint(wp.y));
+                if (NP == 4) stage[w][lane][3] = make_uint4(__float_as_uint(wp.z), 0u, 0u, 0u);
             }
             dest[w][lane] = d[r];
             __syncwarp();
-            // lane 4k + q stores part q of record 8 round + k
+            // part u = 32 round + lane: part u % NP of record u / NP, so the NP
+            // lanes of a record store its bytes contiguously
 #pragma unroll
-            for (int round = 0; round < 4; ++round) {
-                const int k = round * 8 + (lane >> 2), q = lane & 3;
+            for (int round = 0; round < NP; ++round) {
+                const int u = round * 32 + lane, k = u / NP, q = u % NP;
                 const uint32_t dk = dest[w][k];
-                if (dk != kInvalid) bk.r[4 * (size_t)dk + q] = stage[w][k][q];
+                if (dk != kInvalid) bk.r[(size_t)NP * dk + q] = stage[w][k][q];
             }
             __syncwarp();
         }
@@ -250,54 +251,54 @@ constexpr int kPutUnroll = 2;      // kept records in flight per thread (queue w
 
 // Writes kept records (bucket position src, queue slot dst, sequence number)
 // field by field, the loads of each field issued together.
-template <int CT>
+template <int CT, int NP>
 __device__ __forceinline__ void put_entries(const Bucket &bk, uint32_t c0, uint32_t (&src)[kPutUnroll],
                                             const size_t (&dst)[kPutUnroll], const uint32_t (&seq)[kPutUnroll],
                                             const Queues &q, const DebugCheck &dc) {
 #pragma unroll
     for (int r = 0; r < kPutUnroll; ++r)   // dc.cap: bucket records; q.nslots: queue slots
         if (src[r] != kInvalid && !AFR_CHECK(c0 + src[r] < dc.cap && dst[r] < q.nslots, dc.derr)) src[r] = kInvalid;
-    uint4 a[kPutUnroll], q1[kPutUnroll];
+    uint4 a[kPutUnroll], q2[kPutUnroll];
 #pragma unroll
     for (int r = 0; r < kPutUnroll; ++r)
         if (src[r] != kInvalid) {
-            a[r] = bk.r[4 * (size_t)(c0 + src[r])];
-            q1[r] = bk.r[4 * (size_t)(c0 + src[r]) + 1];
+            a[r] = bk.r[(size_t)NP * (c0 + src[r])];
+            q2[r] = bk.r[(size_t)NP * (c0 + src[r]) + 2];
         }
 #pragma unroll
     for (int r = 0; r < kPutUnroll; ++r)
         if (src[r] != kInvalid) {
             q.xy[dst[r]] = make_float2(__uint_as_float(a[r].x), __uint_as_float(a[r].y));
             q.t[dst[r]] = __uint_as_float(a[r].z);
-            q.depth[dst[r]] = __uint_as_float(a[r].w);
+            q.depth[dst[r]] = __uint_as_float(q2[r].y);
             q.seq[dst[r]] = seq[r];
         }
     uint4 bb[kPutUnroll];
 #pragma unroll
     for (int r = 0; r < kPutUnroll; ++r)
-        if (src[r] != kInvalid) bb[r] = bk.r[4 * (size_t)(c0 + src[r]) + 2];
+        if (src[r] != kInvalid) bb[r] = bk.r[(size_t)NP * (c0 + src[r]) + 1];
 #pragma unroll
     for (int r = 0; r < kPutUnroll; ++r)
         if (src[r] != kInvalid) {
             if (CT == AFR_F32) {
                 reinterpret_cast<float4 *>(q.col)[dst[r]] =
                     make_float4(__uint_as_float(bb[r].x), __uint_as_float(bb[r].y), __uint_as_float(bb[r].z), 0.f);
-                q.mo[dst[r]] = make_float2(__uint_as_float(bb[r].w), __uint_as_float(q1[r].y));
+                q.mo[dst[r]] = make_float2(__uint_as_float(bb[r].w), __uint_as_float(q2[r].x));
             } else {
                 reinterpret_cast<ushort4 *>(q.col)[dst[r]] =
                     make_ushort4((unsigned short)(bb[r].x & 0xFFFFu), (unsigned short)(bb[r].x >> 16),
                                  (unsigned short)bb[r].y, 0);
                 q.mo[dst[r]] = make_float2(__uint_as_float(bb[r].z), __uint_as_float(bb[r].w));
             }
-            if (q.world) {
-                const uint4 q3 = bk.r[4 * (size_t)(c0 + src[r]) + 3];
-                q.world[dst[r]] = make_float4(__uint_as_float(q1[r].z), __uint_as_float(q1[r].w),
+            if (NP == 4 && q.world) {
+                const uint4 q3 = bk.r[(size_t)NP * (c0 + src[r]) + 3];
+                q.world[dst[r]] = make_float4(__uint_as_float(q2[r].z), __uint_as_float(q2[r].w),
                                               __uint_as_float(q3.x), 0.f);
             }
         }
 }
 
-template <int CT>
+template <int CT, int NP>
 __global__ void __launch_bounds__(kCommitThreads, 2) k_cell_commit(const uint32_t *__restrict__ coff, int W, int H,
                                                                    int ncx, int b, uint32_t seq0, Bucket bk, Queues q,
                                                                    DebugCheck dc) {
@@ -328,7 +329,8 @@ __global__ void __launch_bounds__(kCommitThreads, 2) k_cell_commit(const uint32_
     if (multi) {
         // per-pixel totals, to group the pixels into rounds
         for (uint32_t j = tid; j < nc; j += kCommitThreads) {
-            const uint32_t l = local_of(bk.r[4 * (size_t)(c0 + j) + 1].x, bk.r[4 * (size_t)(c0 + j)]);
+            const uint4 a = bk.r[(size_t)NP * (c0 + j)];
+            const uint32_t l = local_of(a.w, a);
             if (l < kCellPix) atomicAdd(&sm.total[l], 1u);
         }
         __syncthreads();
@@ -341,9 +343,8 @@ __global__ void __launch_bounds__(kCommitThreads, 2) k_cell_commit(const uint32_
                 const uint32_t j = base + (uint32_t)lane;
                 unsigned long long key = 0ull;
                 if (j < nc) {
-                    const uint32_t i = bk.r[4 * (size_t)(c0 + j) + 1].x;
-                    if (local_of(i, bk.r[4 * (size_t)(c0 + j)]) == (uint32_t)l)
-                        key = ((unsigned long long)(i + 1u) << 32) | j;
+                    const uint4 a = bk.r[(size_t)NP * (c0 + j)];
+                    if (local_of(a.w, a) == (uint32_t)l) key = ((unsigned long long)(a.w + 1u) << 32) | j;
                 }
                 top = warp_top32(top, key);
             }
@@ -358,7 +359,7 @@ __global__ void __launch_bounds__(kCommitThreads, 2) k_cell_commit(const uint32_
                 seq[0] = seq0 + (uint32_t)(top >> 32) - 1u;
                 dst[0] = pixel_of(l) * ub + ((sm.state[l] >> 16) + rank) % ub;
             }
-            put_entries<CT>(bk, c0, src, dst, seq, q, dc);
+            put_entries<CT, NP>(bk, c0, src, dst, seq, q, dc);
         }
     }
     uint32_t group_begin = 0;
@@ -390,8 +391,8 @@ __global__ void __launch_bounds__(kCommitThreads, 2) k_cell_commit(const uint32_
                 const uint32_t j = base + tid + r * kCommitThreads;
                 ii[r] = kInvalid;
                 if (j < nc) {
-                    aa[r] = bk.r[4 * (size_t)(c0 + j)];
-                    ii[r] = bk.r[4 * (size_t)(c0 + j) + 1].x;
+                    aa[r] = bk.r[(size_t)NP * (c0 + j)];
+                    ii[r] = aa[r].w;
                 }
             }
 #pragma unroll
@@ -474,7 +475,7 @@ __global__ void __launch_bounds__(kCommitThreads, 2) k_cell_commit(const uint32_
                 seq[r] = seq0 + me;
                 dst[r] = pixel_of(l) * ub + ((sm.state[l] >> 16) + rank) % ub;
             }
-            put_entries<CT>(bk, c0, src, dst, seq, q, dc);
+            put_entries<CT, NP>(bk, c0, src, dst, seq, q, dc);
         }
         // more than 32: a warp keeps the newest 32 by bitonic merges of the
         // pixel's records, 32 at a time
@@ -502,7 +503,7 @@ __global__ void __launch_bounds__(kCommitThreads, 2) k_cell_commit(const uint32_
                 seq[0] = seq0 + sm.sidx[u];
                 dst[0] = pixel_of(l) * ub + ((sm.state[l] >> 16) + rank) % ub;
             }
-            put_entries<CT>(bk, c0, src, dst, seq, q, dc);
+            put_entries<CT, NP>(bk, c0, src, dst, seq, q, dc);
         }
         __syncthreads();
         group_begin = ge;
@@ -524,11 +525,11 @@ cudaError_t run(AfrContext *c, const float4 *pos, const void *col, const float2 
     const int ncx = (c->W + kCellW - 1) / kCellW;
     const int nkeys = c->ncells * kSubBuckets;
     const DebugCheck dc{(uint32_t)c->batch_cap, c->derr};
-    Bucket bk{c->bucket, c->r_world != nullptr};
-    static bool attr_set = false;   // per colour type: raise the commit kernel's shared-memory limit once
+    Bucket bk{c->bucket};
+    static bool attr_set = false;   // per colour type: raise the commit kernels' shared-memory limit once
     cudaError_t e = cudaSuccess;
     if (!attr_set) {
-        e = cudaFuncSetAttribute(k_cell_commit<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_cell_commit<CT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kCommitSmemBytes);
         if (e != cudaSuccess) return e;
         attr_set = true;
@@ -539,11 +540,12 @@ cudaError_t run(AfrContext *c, const float4 *pos, const void *col, const float2 
     k_cell_count<<<g, 256, 0, s>>>(pos, n, c->W, c->H, ncx, c->ccnt);
     if ((e = scan_exclusive(c->ccnt, c->coff, nkeys, c->scan_tmp, s)) != cudaSuccess) return e;
     const int gs = grid_for((n + kScatterUnroll - 1) / kScatterUnroll, 32 * kScatterWarps);
-    k_cell_scatter<CT><<<gs, 32 * kScatterWarps, 0, s>>>(pos, col, mo, world, n, c->W, c->H, ncx, c->coff, c->ccur,
-                                                          bk, c->fifo_n ? c->fifo_flag : nullptr, c->dcount, dc);
+    uint32_t *accept = c->fifo_n ? c->fifo_flag : nullptr;
     Queues q{c->r_xy, c->r_mo, c->r_t, c->r_depth, c->r_seq, c->r_col, c->r_state, c->r_world, c->nslots};
-    k_cell_commit<CT><<<c->ncells, kCommitThreads, kCommitSmemBytes, s>>>(c->coff, c->W, c->H, ncx, c->b, seq0, bk, q,
-                                                                          dc);
+    k_cell_scatter<CT, 4><<<gs, 32 * kScatterWarps, 0, s>>>(pos, col, mo, c->r_world ? world : nullptr, n, c->W, c->H,
+                                                             ncx, c->coff, c->ccur, bk, accept, c->dcount, dc);
+    k_cell_commit<CT, 4><<<c->ncells, kCommitThreads, kCommitSmemBytes, s>>>(c->coff, c->W, c->H, ncx, c->b, seq0, bk,
+                                                                             q, dc);
     return cudaGetLastError();
 }
 

@@ -8,11 +8,11 @@
 //          aggregated) and keeps the smallest a^2 per bin (the filter's
 //          exponent shift).
 //  scan:   bin offsets.
-//  list:   same slot walk; each moved sample writes its slot index into its
-//          bin's list (unordered, 4 bytes a sample).
+//  list:   same slot walk; each moved sample writes its slot index and its
+//          sequence number into its bin's lists (unordered, 8 bytes a sample).
 //  place:  thread per frame record, in bin order: the slot of list entry e
-//          is moved again, its rank in the bin is the number of the bin's
-//          slots with a smaller sequence number (sequence numbers are
+//          is moved again, its rank in the bin is the number of sequence
+//          numbers in the bin's list below its own (sequence numbers are
 //          unique), and it writes (x', y', a^2, bin column), its colour and its
 //          sequence number to the bin's offset + rank. The lanes of a warp
 //          mostly share a bin, so the rank scans are broadcast reads and the
@@ -157,14 +157,18 @@ __global__ void __launch_bounds__(256) k_list(uint32_t nslots, int b, int bshift
                                               Camera cam, const float4 *__restrict__ world,
                                               const uint32_t *__restrict__ state, const float2 *__restrict__ r_xy,
                                               const float2 *__restrict__ r_mo, const float *__restrict__ r_t,
-                                              const uint32_t *__restrict__ foff, uint32_t *__restrict__ fcur,
-                                              uint32_t *__restrict__ flist, DebugCheck dc) {
+                                              const uint32_t *__restrict__ r_seq, const uint32_t *__restrict__ foff,
+                                              uint32_t *__restrict__ fcur, uint32_t *__restrict__ flist,
+                                              uint32_t *__restrict__ flseq, DebugCheck dc) {
     const uint32_t nlive = FIFO ? min(__ldg(state), nslots) : 0u;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nslots; i += gridDim.x * blockDim.x) {
         Moved mv;
         if (!live_move<FIFO, CAM>(i, nlive, b, bshift, W, H, t_now, cam, world, state, r_xy, r_mo, r_t, mv)) continue;
         const uint32_t at = __ldg(foff + mv.bin) + agg_inc(fcur, mv.bin);
-        if (AFR_CHECK(at < dc.cap, dc.derr)) flist[at] = i;
+        if (AFR_CHECK(at < dc.cap, dc.derr)) {
+            flist[at] = i;
+            flseq[at] = __ldg(r_seq + i);
+        }
     }
 }
 
@@ -176,7 +180,8 @@ __global__ void __launch_bounds__(256) k_place(int W, int H, float t_now, Camera
                                                const float *__restrict__ r_t, const uint32_t *__restrict__ r_seq,
                                                const void *__restrict__ r_col, uint32_t P,
                                                const uint32_t *__restrict__ foff, const uint32_t *__restrict__ flist,
-                                               uint32_t *__restrict__ fcnt, float4 *__restrict__ fpos,
+                                               const uint32_t *__restrict__ flseq, uint32_t *__restrict__ fcnt,
+                                               float4 *__restrict__ fpos,
                                                void *__restrict__ fcol, uint32_t *__restrict__ fseq,
                                                unsigned long long *__restrict__ dcount, DebugCheck dc, uint32_t nsrc) {
     using CS = ColorStore<CT>;
@@ -187,11 +192,11 @@ __global__ void __launch_bounds__(256) k_place(int W, int H, float t_now, Camera
         if (!AFR_CHECK(i < nsrc, dc.derr)) continue;
         const Moved mv = CAM ? move_camera(__ldg(world + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H, cam)
                              : move_sample(__ldg(r_xy + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H);
-        const uint32_t sq = __ldg(r_seq + i);
+        const uint32_t sq = __ldg(flseq + e);
         const uint32_t beg = __ldg(foff + mv.bin), end = __ldg(foff + mv.bin + 1);
         uint32_t rank = 0;
         if (end - beg <= (uint32_t)kSortedBinMax) {
-            for (uint32_t k = beg; k < end; ++k) rank += __ldg(r_seq + __ldg(flist + k)) < sq;
+            for (uint32_t k = beg; k < end; ++k) rank += __ldg(flseq + k) < sq;
         } else {
             rank = atomicSub(fcnt + mv.bin, 1u) - 1u;
             if (rank == 0) atomicAdd(dcount + CNT_UNSORTED, 1ull);
@@ -241,8 +246,8 @@ cudaError_t launch_reproject(AfrContext *c, float t_now, const Camera *camp, cud
     if ((e = scan_exclusive(c->fcnt, c->foff, c->P, c->scan_tmp, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->fcnt, 0, sizeof(uint32_t) * c->P, s)) != cudaSuccess) return e;
 #define AFR_LIST(F_, C_)                                                                                       \
-    k_list<F_, C_><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, cm, wp, state, xy, mo, tt, c->foff,  \
-                                     c->fcnt, c->flist, dc)
+    k_list<F_, C_><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, cm, wp, state, xy, mo, tt, sq, c->foff, \
+                                     c->fcnt, c->flist, c->flseq, dc)
     if (fifo && cam) AFR_LIST(true, true);
     else if (fifo) AFR_LIST(true, false);
     else if (cam) AFR_LIST(false, true);
@@ -250,7 +255,7 @@ cudaError_t launch_reproject(AfrContext *c, float t_now, const Camera *camp, cud
 #undef AFR_LIST
 #define AFR_PLACE(CT_, F_, C_)                                                                                     \
     k_place<CT_, F_, C_><<<g, 256, 0, s>>>(c->W, c->H, t_now, cm, wp, xy, mo, tt, sq, col, (uint32_t)c->P, c->foff, \
-                                           c->flist, c->fcnt, c->fpos, c->fcol, c->fseq, c->dcount, dc, ns)
+                                           c->flist, c->flseq, c->fcnt, c->fpos, c->fcol, c->fseq, c->dcount, dc, ns)
 #define AFR_REPROJ(CT_)                                                                                        \
     do {                                                                                                       \
         if (fifo && cam) AFR_PLACE(CT_, true, true);                                                           \
