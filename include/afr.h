@@ -240,7 +240,8 @@ AFR_API AfrStatus afr_tile_error(AfrContext *ctx, float kappa, float lambda, flo
  * gradient with respect to each output (r, g, b); its 4th lane is ignored
  * (W is treated as a constant). Writes grad_colors_dev (3 floats per
  * frame-view record, frame order; AfrInfo.frame records) and grad_params_dev
- * (6 floats, AfrParams order, summed in double precision). Gradients and
+ * (6 floats, AfrParams order; the per-block partials are added with
+ * compensated FP32 sums). Gradients and
  * densities are held fixed. Weight sums are recomputed, not stored. Requires
  * a preceding afr_reconstruct on the current frame view; its params and
  * t_now are reused. Either output pointer may be NULL to skip it. */

@@ -156,7 +156,7 @@ struct AfrContext {
 
     // backward scratch
     float4 *bgrad = nullptr;      // [P] per-pixel (g_r/S, g_g/S, g_b/S, valid)
-    double *bparam = nullptr;     // [n_bblocks * 6]
+    float *bparam = nullptr;      // [n_bblocks * 6] per-block parameter-gradient partials
     int n_bblocks = 0;
 
     unsigned long long *dcount = nullptr;  // [CNT_N]

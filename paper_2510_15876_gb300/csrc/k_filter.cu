@@ -605,7 +605,7 @@ __global__ void __launch_bounds__(128) k_bwd_pixel(int W, int H, int R, int S_, 
                                                    const uint32_t *__restrict__ foff, const float4 *__restrict__ fpos,
                                                    const void *__restrict__ fcol, const float4 *__restrict__ gout,
                                                    float4 *__restrict__ bg, float4 *__restrict__ bframe,
-                                                   double *__restrict__ bparam) {
+                                                   float *__restrict__ bparam) {
     using CS = ColorStore<CT>;
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -671,8 +671,8 @@ __global__ void __launch_bounds__(128) k_bwd_pixel(int W, int H, int R, int S_, 
     }
     __syncthreads();
     if (tid < 6) {
-        double acc = 0.0;
-        for (int w = 0; w < 4; ++w) acc += (double)sh[tid][w];
+        float acc = 0.f;
+        for (int w = 0; w < 4; ++w) acc += sh[tid][w];
         bparam[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 6 + tid] = acc;
     }
 }
@@ -714,12 +714,34 @@ __global__ void __launch_bounds__(256) k_bwd_record(int W, int H, int R, const u
     }
 }
 
-__global__ void k_bwd_params(const double *__restrict__ part, int nblocks, float *__restrict__ out) {
-    int k = threadIdx.x;
+// The six parameter gradients summed over the blocks' partials: one warp per
+// parameter, each lane a compensated (Kahan) FP32 sum over a strided share of
+// the blocks, then the 32 lane sums (value and compensation) added in a fixed
+// order by lane 0.
+__global__ void k_bwd_params(const float *__restrict__ part, int nblocks, float *__restrict__ out) {
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (k >= 6) return;
-    double acc = 0.0;
-    for (int i = 0; i < nblocks; ++i) acc += part[(size_t)i * 6 + k];
-    out[k] = (float)acc;
+    float s = 0.f, c = 0.f;
+    for (int i = lane; i < nblocks; i += 32) {
+        const float y = part[(size_t)i * 6 + k] - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __shared__ float ss[6][32], cs[6][32];
+    ss[k][lane] = s;
+    cs[k][lane] = c;
+    __syncwarp();
+    if (lane == 0) {
+        float S = 0.f, C = 0.f;
+        for (int l = 0; l < 32; ++l) {
+            const float y = ss[k][l] - cs[k][l] - C;
+            const float t = S + y;
+            C = (t - S) - y;
+            S = t;
+        }
+        out[k] = S;
+    }
 }
 
 template <int CT>
@@ -817,7 +839,7 @@ cudaError_t launch_backward(AfrContext *c, const float4 *grad_rgb, float *grad_c
     if (grad_col)
         k_bwd_record<<<grid_for((size_t)c->P * c->b, 256), 256, 0, s>>>(c->W, c->H, c->R, c->foff, c->fpos, c->bgrad,
                                                                         bframe, grad_col);
-    if (grad_prm) k_bwd_params<<<1, 32, 0, s>>>(c->bparam, (int)(grid.x * grid.y), grad_prm);
+    if (grad_prm) k_bwd_params<<<1, 6 * 32, 0, s>>>(c->bparam, (int)(grid.x * grid.y), grad_prm);
     return cudaGetLastError();
 }
 
