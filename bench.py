@@ -639,10 +639,14 @@ def run_fifo_compare(args, dev):
 
 def run_batched(args, dev, n_streams: int = 48):
     """48 viewer streams (seeds 0-47; sizes, depths and disc counts drawn per
-    stream), FP16 colours, each tuned by the autotuner. The batched step is
-    every stream's gradients and reprojection plus one persistent
-    afr_batch_reconstruct launch, captured in a CUDA graph; the baseline is the
-    same work as 48 sequential single-stream launch sequences."""
+    stream), FP16 colours, each tuned by the autotuner. A step is every
+    stream's gradients, reprojection, widths and filter. Timed forms:
+    afr_batch_refresh (every context on the batch's worker streams) captured
+    in a CUDA graph; the per-stream gradients and reprojection followed by one
+    afr_batch_reconstruct, in a graph; and, as the baseline, the same work as
+    48 sequential single-stream call sequences, eager and in a graph. The
+    per-resolution breakdown times the sequential calls and the refresh graph
+    on each resolution's streams alone."""
     import torch
     from paper_2510_15876_gb300 import autotune
     from paper_2510_15876_gb300.api import BatchReconstructor, Reconstructor
@@ -662,22 +666,9 @@ def run_batched(args, dev, n_streams: int = 48):
     torch.cuda.synchronize()
     gen_s = time.time() - t0
     tuned = [autotune.tune(r, T_NOW) for r in recs]
-    B = BatchReconstructor(recs)
-    outs = [torch.empty((r.H, r.W, 4), dtype=torch.float32, device=dev) for r in recs]
+    k = max(3, args.steps // 4)
 
-    def batched_step():
-        for r in recs:
-            r.estimate_gradients(T_NOW)
-            r.reproject(T_NOW)
-        B.run(T_NOW)
-
-    def sequential_step():
-        for r, o in zip(recs, outs):
-            r.estimate_gradients(T_NOW)
-            r.reproject(T_NOW)
-            r.reconstruct(T_NOW, out=o)
-
-    def timed(fn, k):
+    def timed(fn):
         for _ in range(2):
             fn()
         torch.cuda.synchronize()
@@ -689,33 +680,83 @@ def run_batched(args, dev, n_streams: int = 48):
         torch.cuda.synchronize()
         return s.elapsed_time(e) / k
 
-    k = max(3, args.steps // 4)
-    seq_ms = timed(sequential_step, k)
-    batch_ms = timed(batched_step, k)
-    side = torch.cuda.Stream()
-    side.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(side):
-        batched_step()
-    torch.cuda.current_stream().wait_stream(side)
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        batched_step()
-    graph_ms = timed(g.replay, k)
-    status = [r.status() for r in recs]
+    def graphed(fn):
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            fn()
+        torch.cuda.current_stream().wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        return g
+
+    def forms(group):
+        outs = [torch.empty((r.H, r.W, 4), dtype=torch.float32, device=dev) for r in group]
+        B = BatchReconstructor(group)
+
+        def sequential_step():
+            for r, o in zip(group, outs):
+                r.estimate_gradients(T_NOW)
+                r.reproject(T_NOW)
+                r.reconstruct(T_NOW, out=o)
+
+        def persistent_step():
+            for r in group:
+                r.estimate_gradients(T_NOW)
+                r.reproject(T_NOW)
+            B.run(T_NOW)
+
+        def refresh_step():
+            B.refresh(T_NOW)
+
+        t = {"sequential": timed(sequential_step)}
+        g_seq = graphed(sequential_step)
+        t["sequential_graph"] = timed(g_seq.replay)
+        t["refresh"] = timed(refresh_step)
+        g_ref = graphed(refresh_step)
+        t["refresh_graph"] = timed(g_ref.replay)
+        g_per = graphed(persistent_step)
+        t["persistent_graph"] = timed(g_per.replay)
+        same = all(torch.equal(a, b) for a, b in zip(outs, B.outs))
+        del g_seq, g_ref, g_per
+        B.close()
+        return t, same
+
+    t_all, same_all = forms(recs)
     pixels = sum(r.W * r.H for r in recs)
+    per_res = {}
+    for key in sorted({(r.W, r.H) for r in recs}, key=lambda wh: wh[0] * wh[1]):
+        group = [r for r in recs if (r.W, r.H) == key]
+        tg, same = forms(group)
+        same_all = same_all and same
+        per_res[f"{key[0]}x{key[1]}"] = {
+            "streams": len(group), "depths": sorted({r.b for r in group}),
+            "sequential_ms": round(tg["sequential"], 3), "sequential_graph_ms": round(tg["sequential_graph"], 3),
+            "refresh_graph_ms": round(tg["refresh_graph"], 3),
+            "speedup_vs_sequential": round(tg["sequential"] / tg["refresh_graph"], 2)}
+    status = [r.status() for r in recs]
+    best = min(t_all["refresh_graph"], t_all["persistent_graph"])
     res = {
         "streams": n_streams, "pixels": pixels, "samples": sum(r.W * r.H * r.b for r in recs),
-        "graph_ms_per_step": round(graph_ms, 3), "batched_ms_per_step": round(batch_ms, 3),
-        "sequential_ms_per_step": round(seq_ms, 3),
-        "mpixel_per_s_graph": round(pixels / graph_ms / 1e3, 1),
-        "mpixel_per_s_sequential": round(pixels / seq_ms / 1e3, 1),
+        "refresh_graph_ms_per_step": round(t_all["refresh_graph"], 3),
+        "refresh_ms_per_step": round(t_all["refresh"], 3),
+        "persistent_graph_ms_per_step": round(t_all["persistent_graph"], 3),
+        "sequential_ms_per_step": round(t_all["sequential"], 3),
+        "sequential_graph_ms_per_step": round(t_all["sequential_graph"], 3),
+        "mpixel_per_s_batched": round(pixels / best / 1e3, 1),
+        "mpixel_per_s_sequential": round(pixels / t_all["sequential"] / 1e3, 1),
+        "speedup_vs_sequential": round(t_all["sequential"] / best, 2),
+        "speedup_vs_sequential_graph": round(t_all["sequential_graph"] / best, 2),
+        "per_resolution": per_res,
         "radius_counts": {str(rr): sum(1 for t in tuned if t[0] == rr) for rr in autotune.RADII},
         "tile_counts": {str(tt): sum(1 for t in tuned if t[1] == tt) for tt in autotune.TILES},
+        "images_identical": bool(same_all),
         "status_ok": all(s_ == 0 for s_ in status), "generation_s": round(gen_s, 1),
-        "what": "per stream afr_estimate_gradients + afr_reproject, then one afr_batch_reconstruct (CUDA graph) "
-                "vs per stream afr_reconstruct launches",
+        "what": "every stream's gradients, reprojection, widths and filter: afr_batch_refresh on worker streams "
+                "(CUDA graph), or per stream gradients + reprojection then one afr_batch_reconstruct (graph), "
+                "vs the per stream calls in series",
     }
-    B.close()
     for r in recs:
         r.close()
     torch.cuda.empty_cache()

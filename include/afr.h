@@ -380,6 +380,19 @@ AFR_API void afr_batch_destroy(AfrBatch *batch);
 AFR_API AfrStatus afr_batch_reconstruct(AfrBatch *batch, float t_now, const AfrParams *params,
                                         float *const *outs_dev, afr_stream_t stream);
 
+/* The whole refresh of every context of the batch in one call: for each,
+ * afr_estimate_gradients, afr_reproject and afr_reconstruct at t_now with
+ * params, its image to outs_dev[i]. The contexts are spread over the batch's
+ * own worker streams (fixed at afr_batch_create: four, each context on the
+ * one with the least buffered work so far, largest contexts first), which
+ * wait for the work issued on stream before the call and which stream waits
+ * for after it, so independent contexts run concurrently and the call can be
+ * captured in a CUDA graph. Results equal the calls in series bit for bit.
+ * Reads each context's sample buffers: the same ordering rules as the calls
+ * it stands for. */
+AFR_API AfrStatus afr_batch_refresh(AfrBatch *batch, float t_now, const AfrParams *params,
+                                    float *const *outs_dev, afr_stream_t stream);
+
 /* ---------------------------------------------------------------------
  * Allocation-free variant (no counterpart in the paper).
  * --------------------------------------------------------------------- */

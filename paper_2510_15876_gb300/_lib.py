@@ -31,6 +31,7 @@ EXPORTED = [
     "afr_export_map", "afr_import_map", "afr_set_frame_colors", "afr_reproject_batch_static", "afr_set_tuning",
     "afr_profile_filter", "afr_profile_read", "afr_tile_error", "afr_reproject_camera",
     "afr_batch_create", "afr_batch_destroy", "afr_batch_reconstruct", "afr_measure_alu_peaks",
+    "afr_batch_refresh",
 ]
 
 
@@ -99,6 +100,7 @@ def _declare(L):
         "afr_batch_destroy": (None, [c_p]),
         "afr_batch_reconstruct": (S, [c_p, c_f32, ctypes.POINTER(AfrParams), ctypes.POINTER(c_p), c_p]),
         "afr_measure_alu_peaks": (S, [c_p]),
+        "afr_batch_refresh": (S, [c_p, c_f32, ctypes.POINTER(AfrParams), ctypes.POINTER(c_p), c_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

@@ -315,6 +315,15 @@ class BatchReconstructor:
             raise L.AfrError(st, "afr_batch_reconstruct failed")
         return self.outs
 
+    def refresh(self, t_now: float = 1.0, params=None, stream=None) -> list[torch.Tensor]:
+        """afr_batch_refresh: gradients, reprojection and filter of every
+        context, spread over the batch's worker streams."""
+        prm = _params(params)
+        st = self.lib.afr_batch_refresh(self.h, t_now, ctypes.byref(prm), self._ptrs, _stream(stream))
+        if st != L.AFR_OK:
+            raise L.AfrError(st, "afr_batch_refresh failed")
+        return self.outs
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.afr_batch_destroy(self.h)

@@ -145,6 +145,12 @@ struct AfrBatch {
     uint32_t total = 0;              // work items of the persistent kernel (tiles of the other contexts)
     uint32_t nchunks = 0;            // width chunks of the other contexts
     int ct = 0, grid = 0;
+    // afr_batch_refresh: worker streams forked from and joined to the caller's
+    // stream, and each context's worker (longest-processing-time first)
+    std::vector<cudaStream_t> workers;
+    std::vector<cudaEvent_t> joined;
+    cudaEvent_t forked = nullptr;
+    std::vector<int> worker_of;      // per queue position
 };
 
 extern "C" {
@@ -721,6 +727,9 @@ void afr_batch_destroy(AfrBatch *b) {
     if (b->h_ctx) cudaFreeHost(b->h_ctx);
     if (b->d_ctx) cudaFree(b->d_ctx);
     if (b->d_queue) cudaFree(b->d_queue);
+    for (cudaStream_t w : b->workers) cudaStreamDestroy(w);
+    for (cudaEvent_t e : b->joined) cudaEventDestroy(e);
+    if (b->forked) cudaEventDestroy(b->forked);
     delete b;
 }
 
@@ -770,10 +779,71 @@ AfrStatus afr_batch_create(AfrContext *const *ctxs, int32_t n, AfrBatch **out) {
         return e == cudaErrorMemoryAllocation ? AFR_ERR_OOM : AFR_ERR_CUDA;
     }
     b->grid = 3 * sms;
+    // afr_batch_refresh: kBatchWorkers streams, each context on the one with
+    // the least work so far (work ~ its buffered slots), largest first
+    const int nw = std::min(n, afr::kBatchWorkers);
+    std::vector<double> load(nw, 0.0);
+    for (int q = 0; q < n; ++q) {
+        const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        b->worker_of.push_back(w);
+        load[w] += (double)b->ctxs[q]->P * (b->ctxs[q]->b + 8);
+    }
+    for (int w = 0; w < nw && e == cudaSuccess; ++w) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) b->workers.push_back(st);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->joined.push_back(ev);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->forked, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        afr_batch_destroy(b);
+        return AFR_ERR_CUDA;
+    }
     *out = b;
     return AFR_OK;
 }
 
+
+AfrStatus afr_batch_refresh(AfrBatch *b, float t_now, const AfrParams *params, float *const *outs_dev,
+                            afr_stream_t stream) {
+    Range nvtx_range("afr_batch_refresh");
+    if (!b || !params || !outs_dev || !std::isfinite(t_now)) return AFR_ERR_INVALID_ARG;
+    if (!params_ok(params)) return AFR_ERR_INVALID_ARG;
+    const int n = (int)b->ctxs.size();
+    for (int q = 0; q < n; ++q) {
+        float *o = outs_dev[b->user_index[q]];
+        if (!o || !aligned(o, 16))
+            return fail(b->ctxs[q], AFR_ERR_INVALID_ARG, "afr_batch_refresh: bad output pointer");
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaEventRecord(b->forked, s);
+    for (size_t w = 0; w < b->workers.size() && e == cudaSuccess; ++w) e = cudaStreamWaitEvent(b->workers[w], b->forked, 0);
+    for (int q = 0; q < n && e == cudaSuccess; ++q) {
+        AfrContext *c = b->ctxs[q];
+        cudaStream_t ws = b->workers[b->worker_of[q]];
+        e = afr::launch_gradients(c, t_now, ws);
+        if (e == cudaSuccess) e = afr::launch_reproject(c, t_now, nullptr, ws);
+        if (e == cudaSuccess) e = afr::launch_sigma(c, params, false, false, ws);
+        if (e == cudaSuccess)
+            e = afr::launch_filter(c, t_now, false, reinterpret_cast<float4 *>(outs_dev[b->user_index[q]]), ws);
+    }
+    for (size_t w = 0; w < b->workers.size() && e == cudaSuccess; ++w) {
+        e = cudaEventRecord(b->joined[w], b->workers[w]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->joined[w], 0);
+    }
+    if (e != cudaSuccess) return cuda_fail(b->ctxs[0], e, "afr_batch_refresh");
+    for (AfrContext *c : b->ctxs) {
+        c->grads_valid = c->frame_valid = c->recon_valid = true;
+        c->grads_t = c->frame_t = c->recon_t = t_now;
+        c->recon_params = *params;
+        c->sigma_imported = false;
+        c->adaptive_last = false;
+    }
+    return AFR_OK;
+}
 
 AfrStatus afr_batch_reconstruct(AfrBatch *b, float t_now, const AfrParams *params, float *const *outs_dev,
                                 afr_stream_t stream) {

@@ -361,6 +361,7 @@ cudaError_t launch_batch(int ct, const BatchCtx *cs, int nctx, uint32_t nchunks,
                          int grid, cudaStream_t s);
 constexpr int kBatchSigmaChunk = 2048;   // pixels per width chunk of a batched launch
 constexpr int kBatchDirectPixels = 131072;   // larger contexts of a batch get their own launches
+constexpr int kBatchWorkers = 4;             // streams of afr_batch_refresh
 cudaError_t launch_resident_count(AfrContext *c, cudaStream_t s);
 int ingest_sub_buckets();
 

@@ -75,7 +75,7 @@ def test_batch_against_oracle_at_chosen_radius(dev):
         hole = ref[:, 3] == 0
         assert np.all(got[hole, :3] == 0)
         err = np.abs(got[~hole, :3] - ref[~hole, :3]) / np.maximum(np.abs(ref[~hole, :3]), 1e-3)
-        assert np.quantile(err, 0.999) < 1e-4 and err.max() < 1e-2, (R, np.quantile(err, 0.999), err.max())
+        assert err.max() <= 1e-5, (R, err.max())
     B.close()
 
 
@@ -112,3 +112,39 @@ def test_batch_graph_replay(dev):
         assert torch.equal(a, b)
     assert all(r.status() == L.AFR_OK for r in recs)
     B.close()
+
+
+@pytest.mark.parametrize("streams", [STREAMS, MIXED], ids=["small", "mixed"])
+def test_batch_refresh_matches_calls_in_series(dev, streams):
+    """afr_batch_refresh (gradients, reprojection and filter of every context
+    on the batch's worker streams) gives the images of the calls in series,
+    bit for bit, directly and replayed from a CUDA graph."""
+    from paper_2510_15876_gb300.api import BatchReconstructor
+    recs, _ = _make(dev, streams=streams)
+    want = []
+    for r in recs:
+        r.estimate_gradients(T_NOW)
+        r.reproject(T_NOW)
+        want.append(r.reconstruct(T_NOW).clone())
+    B = BatchReconstructor(recs)
+    outs = B.refresh(T_NOW)
+    torch.cuda.synchronize()
+    for a, b in zip(want, outs):
+        assert torch.equal(a, b)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        B.refresh(T_NOW)
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        B.refresh(T_NOW)
+    for o in B.outs:
+        o.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(want, B.outs):
+        assert torch.equal(a, b)
+    assert all(r.status() == L.AFR_OK for r in recs)
+    B.close()
+
