@@ -189,7 +189,7 @@ AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
     c->csize = c->ct == AFR_F32 ? 16 : 8;
     c->fifo_n = g.fifo_capacity;
     c->frame_cap = std::max(c->nslots, c->fifo_n);
-    c->scan_tmp_n = afr::scan_tmp_elems(std::max<size_t>((size_t)c->P, (size_t)(((c->W + 15) / 16) * ((c->H + 7) / 8)) * 8));
+    c->scan_tmp_n = afr::scan_tmp_elems((size_t)c->P);
     c->n_bblocks = afr::backward_blocks(c->W, c->H);
     cudaError_t e = cudaSuccess;
     size_t P = c->P, N = c->nslots;
@@ -202,8 +202,7 @@ AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
     AFR_ALLOC(c->r_seq, N);
     if (e == cudaSuccess) e = dmalloc(&c->r_col, N * c->csize);
     AFR_ALLOC(c->r_state, P);
-    c->ncells = ((c->W + 15) / 16) * ((c->H + 7) / 8);
-    const size_t nkeys = (size_t)c->ncells * afr::ingest_sub_buckets();
+    const size_t nkeys = P;   // ingest buckets: one per pixel
     AFR_ALLOC(c->ccnt, nkeys);
     AFR_ALLOC(c->coff, nkeys + 1);
     AFR_ALLOC(c->ccur, nkeys);

@@ -117,11 +117,10 @@ struct AfrContext {
     uint32_t *fifo_rank = nullptr;  // [batch_cap + 1] exclusive scan of fifo_flag, then the total
     uint32_t *fifo_scan = nullptr;  // scan block sums for batch_cap entries
     // ingest scratch: per-cell counts and offsets (cells of 16 x 8 pixels) and
-    // the batch's bucket planes in cell order (batch_cap records)
-    int ncells = 0;
-    uint32_t *ccnt = nullptr;     // [ncells * sub-buckets] bucket counts
-    uint32_t *coff = nullptr;     // [ncells * sub-buckets + 1] bucket offsets
-    uint32_t *ccur = nullptr;     // [ncells * sub-buckets] append cursors
+    // the batch's records bucketed by pixel (batch_cap records)
+    uint32_t *ccnt = nullptr;     // [P] bucket counts
+    uint32_t *coff = nullptr;     // [P + 1] bucket offsets
+    uint32_t *ccur = nullptr;     // [P] append cursors, then the queue states before the batch
     uint4 *bucket = nullptr;      // [4 * batch_cap] 64-byte sample records in bucket order
     size_t batch_cap = 0;
 
@@ -363,6 +362,5 @@ constexpr int kBatchSigmaChunk = 2048;   // pixels per width chunk of a batched 
 constexpr int kBatchDirectPixels = 131072;   // larger contexts of a batch get their own launches
 constexpr int kBatchWorkers = 4;             // streams of afr_batch_refresh
 cudaError_t launch_resident_count(AfrContext *c, cudaStream_t s);
-int ingest_sub_buckets();
 
 }  // namespace afr

@@ -3,50 +3,45 @@
 // order).
 //
 // The batch arrives in insertion order with its samples spread over the whole
-// image, and the queues are planes in pixel order, so ingest is a sort. It
-// runs through cells of 16 x 8 pixels:
+// image, and the queues are planes in pixel order, so ingest is a counting
+// sort by pixel followed by a per-pixel selection:
 //
-//  1. count:   per bucket, the samples whose position is valid (reads only
-//              the 16-byte position of each sample). A cell's records go to
-//              kSubBuckets buckets by batch index modulo kSubBuckets, laid out
-//              one after another, so that the cell's bucket is still one
-//              contiguous range while each counter takes one eighth of the
-//              cell's atomics.
-//  2. scan:    bucket offsets.
+//  1. count:   per pixel, the samples whose position is valid (reads only the
+//              16-byte position of each sample).
+//  2. scan:    bucket offsets, one bucket per pixel.
 //  3. scatter: each sample appends its 64-byte record (position, colour,
-//              motion, batch index, hit point) to its bucket. A warp stages its
-//              32 records in shared memory and stores each with four lanes, so
-//              every store is two whole sectors; a thread takes the tickets of
-//              several samples before using any, to keep atomics in flight. A
-//              sample whose colour or motion is not finite leaves a dead
-//              record (batch index kInvalid).
-//  4. commit:  one CTA per cell reads its bucket once, sorts the records by
-//              pixel in shared memory, ranks each pixel's records by batch
-//              index (insertion order) and writes the newest min(b, m) to the
-//              queue slots (head + rank) mod b that sequential pushes would
-//              use, so a warp's stores cover consecutive slots. A cell with
-//              more records than one round of shared memory is committed in
-//              rounds over groups of its pixels; a pixel that alone holds
-//              more is ranked by a warp streaming the bucket and keeping the
-//              newest 32 in registers.
+//              motion, batch index, hit point) to its pixel's bucket. A warp
+//              stages its 32 records in shared memory and stores each with
+//              four lanes, so every store is two whole sectors; a thread takes
+//              the tickets of both its samples before using either. A sample
+//              whose colour or motion is not finite leaves a dead record
+//              (batch index kInvalid).
+//  4. commit:  a thread per bucket record, in bucket (= pixel) order: its
+//              rank among its pixel's live records is the number of them with
+//              a smaller batch index (read from shared memory, where a block
+//              keeps the batch indices of the records it holds); the newest
+//              min(b, m) go to the queue slots
+//              (head + rank) mod b that sequential pushes would use, so a
+//              warp's stores cover consecutive slots. The first record of each
+//              pixel writes the pixel's new queue state (from a copy of the
+//              states taken before the commit, which every thread reads). A
+//              pixel with more than kBigPixel records is left to a warp that
+//              streams its bucket keeping the newest 32 in registers.
 #include "afr_internal.cuh"
 
 namespace afr {
 namespace {
 
-constexpr int kCellW = 16, kCellH = 8, kCellPix = kCellW * kCellH;
-constexpr int kSubBuckets = 8;
-constexpr int kCommitCap = 3072;      // records of one round in shared memory
-constexpr int kCommitThreads = 512;
-constexpr int kCommitWarps = kCommitThreads / 32;
+constexpr uint32_t kBigPixel = 256;   // records of one pixel above which a warp selects the newest b
 
-// Bucket records, NP = 4 uint4 (64 bytes: two whole sectors) each:
+// Bucket records, 4 uint4 (64 bytes: two whole sectors) each:
 //   q0 = (x, y, t, batch index)
 //   q1 = FP32: (r, g, b, m_x); 16-bit: (r | g << 16, b, m_x, m_y)
 //   q2 = (m_y for FP32 colours, depth, hit point X, Y)
 //   q3 = (hit point Z, 0, 0, 0)
-// The first 16 bytes are all the commit's sort reads. (Three-part, 48-byte
-// records, whose halves of a shared sector L2 has to merge, measured slower.)
+// (Three-part, 48-byte records, whose halves of a shared sector L2 has to
+// merge, measured slower.)
+constexpr int NP = 4;
 struct Bucket {
     uint4 *r;    // [NP * batch_cap]
 };
@@ -67,16 +62,15 @@ __device__ __forceinline__ bool position_ok(float4 p, int W, int H) {
            p.y < (float)H;
 }
 
-__device__ __forceinline__ uint32_t cell_of(float x, float y, int ncx) {
-    const int qx = (int)floorf(x), qy = (int)floorf(y);
-    return (uint32_t)((qy / kCellH) * ncx + qx / kCellW);
+__device__ __forceinline__ uint32_t pixel_at(float x, float y, int W) {
+    return (uint32_t)(int)floorf(y) * (uint32_t)W + (uint32_t)(int)floorf(x);
 }
 
-__global__ void __launch_bounds__(256) k_cell_count(const float4 *__restrict__ pos, uint32_t n, int W, int H, int ncx,
-                                                    uint32_t *__restrict__ ccnt) {
+__global__ void __launch_bounds__(256) k_pix_count(const float4 *__restrict__ pos, uint32_t n, int W, int H,
+                                                   uint32_t *__restrict__ pcnt) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float4 p = __ldg(pos + i);
-        if (position_ok(p, W, H)) atomicAdd(ccnt + cell_of(p.x, p.y, ncx) * kSubBuckets + (i & (kSubBuckets - 1)), 1u);
+        if (position_ok(p, W, H)) atomicAdd(pcnt + pixel_at(p.x, p.y, W), 1u);
     }
 }
 
@@ -87,13 +81,13 @@ __device__ __forceinline__ bool sample_ok(float4 p, typename ColorStore<CT>::T c
 }
 
 constexpr int kScatterWarps = 8;
-constexpr int kScatterUnroll = 4;   // samples (and ticket atomics) in flight per thread
+constexpr int kScatterUnroll = 2;   // samples (and ticket atomics) in flight per thread
 
-template <int CT, int NP>
-__global__ void __launch_bounds__(32 * kScatterWarps) k_cell_scatter(
+template <int CT>
+__global__ void __launch_bounds__(32 * kScatterWarps) k_pix_scatter(
     const float4 *__restrict__ pos, const void *__restrict__ col, const float2 *__restrict__ mo,
-    const float4 *__restrict__ world, uint32_t n, int W, int H, int ncx, const uint32_t *__restrict__ coff,
-    uint32_t *__restrict__ ccur, Bucket bk, uint32_t *__restrict__ accept, unsigned long long *__restrict__ dcount,
+    const float4 *__restrict__ world, uint32_t n, int W, int H, const uint32_t *__restrict__ poff,
+    uint32_t *__restrict__ pcur, Bucket bk, uint32_t *__restrict__ accept, unsigned long long *__restrict__ dcount,
     DebugCheck dc) {
     using CS = ColorStore<CT>;
     __shared__ uint4 stage[kScatterWarps][32][5];   // 80-byte stride: conflict-free 16-byte accesses
@@ -126,8 +120,8 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_cell_scatter(
             if (in && accept) accept[i] = ok[r] ? 1u : 0u;
             d[r] = kInvalid;
             if (pok) {
-                const uint32_t key = cell_of(p[r].x, p[r].y, ncx) * kSubBuckets + (i & (kSubBuckets - 1));
-                d[r] = __ldg(coff + key) + atomicAdd(ccur + key, 1u);
+                const uint32_t px = pixel_at(p[r].x, p[r].y, W);
+                d[r] = __ldg(poff + px) + atomicAdd(pcur + px, 1u);
                 if (!AFR_CHECK(d[r] < dc.cap, dc.derr)) d[r] = kInvalid;
             }
         }
@@ -136,7 +130,7 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_cell_scatter(
             const uint32_t i = base + r * 32 + lane;
             if (d[r] != kInvalid) {
                 float4 wp = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (NP == 4 && ok[r] && world) wp = __ldg(world + i);
+                if (ok[r] && world) wp = __ldg(world + i);
                 uint4 q1;
                 uint32_t my = 0u;
                 if (CT == AFR_F32) {
@@ -153,7 +147,7 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_cell_scatter(
                                                __float_as_uint(p[r].z), ok[r] ? i : kInvalid);
                 stage[w][lane][1] = q1;
                 stage[w][lane][2] = make_uint4(my, __float_as_uint(p[r].w), __float_as_uint(wp.x), __float_as_uint(wp.y));
-                if (NP == 4) stage[w][lane][3] = make_uint4(__float_as_uint(wp.z), 0u, 0u, 0u);
+                stage[w][lane][3] = make_uint4(__float_as_uint(wp.z), 0u, 0u, 0u);
             }
             dest[w][lane] = d[r];
             __syncwarp();
@@ -204,354 +198,182 @@ __device__ __forceinline__ unsigned long long warp_top32(unsigned long long top,
     return warp_merge_asc(max(top, rev));
 }
 
-// Shared memory of the commit kernel (dynamic; kCommitCap records a round).
-struct CommitSmem {
-    uint32_t *idx;      // [cap] batch index of round record k
-    uint32_t *src;      // [cap] its bucket position within the cell
-    uint16_t *tick;     // [cap] its arrival rank within its pixel in this round
-    uint8_t *lp;        // [cap] its cell pixel
-    uint32_t *sidx;     // [cap] batch indices in pixel order (sorted position u)
-    uint32_t *ssrc;     // [cap] bucket positions in pixel order
-    uint8_t *slp;       // [cap] cell pixels in pixel order
-    uint32_t *total;    // [kCellPix] the batch's records per pixel
-    uint32_t *count;    // [kCellPix] this round's records per pixel
-    uint32_t *start;    // [kCellPix] first sorted position of each pixel in this round
-    uint32_t *state;    // [kCellPix] queue state of each pixel before the batch
-    uint32_t *misc;     // [2] records gathered in this round, end of this round's pixels
-};
-
-constexpr size_t kCommitSmemBytes =
-    (size_t)kCommitCap * (4 + 4 + 2 + 1 + 4 + 4 + 1) + (size_t)kCellPix * 16 + 16;
-
-__device__ __forceinline__ CommitSmem commit_smem(unsigned char *base) {
-    CommitSmem m;
-    unsigned char *p = base;
-    auto take = [&](size_t bytes) {
-        unsigned char *r = p;
-        p += (bytes + 15) & ~(size_t)15;
-        return r;
-    };
-    m.idx = reinterpret_cast<uint32_t *>(take(4 * kCommitCap));
-    m.src = reinterpret_cast<uint32_t *>(take(4 * kCommitCap));
-    m.sidx = reinterpret_cast<uint32_t *>(take(4 * kCommitCap));
-    m.ssrc = reinterpret_cast<uint32_t *>(take(4 * kCommitCap));
-    m.total = reinterpret_cast<uint32_t *>(take(4 * kCellPix));
-    m.count = reinterpret_cast<uint32_t *>(take(4 * kCellPix));
-    m.start = reinterpret_cast<uint32_t *>(take(4 * kCellPix));
-    m.state = reinterpret_cast<uint32_t *>(take(4 * kCellPix));
-    m.misc = reinterpret_cast<uint32_t *>(take(16));
-    m.tick = reinterpret_cast<uint16_t *>(take(2 * kCommitCap));
-    m.lp = reinterpret_cast<uint8_t *>(take(kCommitCap));
-    m.slp = reinterpret_cast<uint8_t *>(take(kCommitCap));
-    return m;
+// Queue state (count | head << 16) after m more pushes.
+__device__ __forceinline__ uint32_t pushed_state(uint32_t st, uint32_t m, uint32_t ub) {
+    const uint32_t cnt = st & 0xFFFFu, h = st >> 16;
+    const uint32_t cn = (uint64_t)cnt + m < (uint64_t)ub ? cnt + m : ub;
+    const uint32_t hn = (uint32_t)((h + (uint64_t)m) % ub);
+    return cn | (hn << 16);
 }
 
-constexpr int kCommitUnroll = 4;   // bucket records in flight per thread (gather)
-constexpr int kPutUnroll = 2;      // kept records in flight per thread (queue writes)
-
-// Writes kept records (bucket position src, queue slot dst, sequence number)
-// field by field, the loads of each field issued together.
-template <int CT, int NP>
-__device__ __forceinline__ void put_entries(const Bucket &bk, uint32_t c0, uint32_t (&src)[kPutUnroll],
-                                            const size_t (&dst)[kPutUnroll], const uint32_t (&seq)[kPutUnroll],
-                                            const Queues &q, const DebugCheck &dc) {
-#pragma unroll
-    for (int r = 0; r < kPutUnroll; ++r)   // dc.cap: bucket records; q.nslots: queue slots
-        if (src[r] != kInvalid && !AFR_CHECK(c0 + src[r] < dc.cap && dst[r] < q.nslots, dc.derr)) src[r] = kInvalid;
-    uint4 a[kPutUnroll], q2[kPutUnroll];
-#pragma unroll
-    for (int r = 0; r < kPutUnroll; ++r)
-        if (src[r] != kInvalid) {
-            a[r] = bk.r[(size_t)NP * (c0 + src[r])];
-            q2[r] = bk.r[(size_t)NP * (c0 + src[r]) + 2];
-        }
-#pragma unroll
-    for (int r = 0; r < kPutUnroll; ++r)
-        if (src[r] != kInvalid) {
-            q.xy[dst[r]] = make_float2(__uint_as_float(a[r].x), __uint_as_float(a[r].y));
-            q.t[dst[r]] = __uint_as_float(a[r].z);
-            q.depth[dst[r]] = __uint_as_float(q2[r].y);
-            q.seq[dst[r]] = seq[r];
-        }
-    uint4 bb[kPutUnroll];
-#pragma unroll
-    for (int r = 0; r < kPutUnroll; ++r)
-        if (src[r] != kInvalid) bb[r] = bk.r[(size_t)NP * (c0 + src[r]) + 1];
-#pragma unroll
-    for (int r = 0; r < kPutUnroll; ++r)
-        if (src[r] != kInvalid) {
-            if (CT == AFR_F32) {
-                reinterpret_cast<float4 *>(q.col)[dst[r]] =
-                    make_float4(__uint_as_float(bb[r].x), __uint_as_float(bb[r].y), __uint_as_float(bb[r].z), 0.f);
-                q.mo[dst[r]] = make_float2(__uint_as_float(bb[r].w), __uint_as_float(q2[r].x));
-            } else {
-                reinterpret_cast<ushort4 *>(q.col)[dst[r]] =
-                    make_ushort4((unsigned short)(bb[r].x & 0xFFFFu), (unsigned short)(bb[r].x >> 16),
-                                 (unsigned short)bb[r].y, 0);
-                q.mo[dst[r]] = make_float2(__uint_as_float(bb[r].z), __uint_as_float(bb[r].w));
-            }
-            if (NP == 4 && q.world) {
-                const uint4 q3 = bk.r[(size_t)NP * (c0 + src[r]) + 3];
-                q.world[dst[r]] = make_float4(__uint_as_float(q2[r].z), __uint_as_float(q2[r].w),
-                                              __uint_as_float(q3.x), 0.f);
-            }
-        }
+// Writes one kept record (parts a, q1, q2, q3) to queue slot dst.
+template <int CT>
+__device__ __forceinline__ void put_record(const uint4 &a, const uint4 &q1, const uint4 &q2, const uint4 &q3, size_t dst,
+                                           uint32_t seq, const Queues &q) {
+    q.xy[dst] = make_float2(__uint_as_float(a.x), __uint_as_float(a.y));
+    q.t[dst] = __uint_as_float(a.z);
+    q.depth[dst] = __uint_as_float(q2.y);
+    q.seq[dst] = seq;
+    if (CT == AFR_F32) {
+        reinterpret_cast<float4 *>(q.col)[dst] =
+            make_float4(__uint_as_float(q1.x), __uint_as_float(q1.y), __uint_as_float(q1.z), 0.f);
+        q.mo[dst] = make_float2(__uint_as_float(q1.w), __uint_as_float(q2.x));
+    } else {
+        reinterpret_cast<ushort4 *>(q.col)[dst] =
+            make_ushort4((unsigned short)(q1.x & 0xFFFFu), (unsigned short)(q1.x >> 16), (unsigned short)q1.y, 0);
+        q.mo[dst] = make_float2(__uint_as_float(q1.z), __uint_as_float(q1.w));
+    }
+    if (q.world)
+        q.world[dst] = make_float4(__uint_as_float(q2.z), __uint_as_float(q2.w), __uint_as_float(q3.x), 0.f);
 }
 
-template <int CT, int NP>
-__global__ void __launch_bounds__(kCommitThreads, 2) k_cell_commit(const uint32_t *__restrict__ coff, int W, int H,
-                                                                   int ncx, int b, uint32_t seq0, Bucket bk, Queues q,
-                                                                   DebugCheck dc) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const CommitSmem sm = commit_smem(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t cell = blockIdx.x;
-    const uint32_t c0 = coff[cell * kSubBuckets], nc = coff[(cell + 1) * kSubBuckets] - c0;
-    if (nc == 0) return;   // block-uniform
-    const int x0 = (int)(cell % (uint32_t)ncx) * kCellW, y0 = (int)(cell / (uint32_t)ncx) * kCellH;
+// Thread per bucket record, pixels of up to kBigPixel records. A block takes
+// kCommitTile consecutive records at a time and keeps their batch indices in
+// shared memory, where the rank scans find all of a pixel's records but
+// those of pixels crossing the tile's ends. state0 holds the queue states
+// before the batch.
+constexpr int kCommitTile = 256;
+
+template <int CT>
+__global__ void __launch_bounds__(kCommitTile) k_pix_commit(const uint32_t *__restrict__ poff, uint32_t P, int W,
+                                                            int b, uint32_t seq0, Bucket bk, Queues q,
+                                                            const uint32_t *__restrict__ state0, DebugCheck dc) {
+    __shared__ uint32_t sidx[kCommitTile];
+    uint32_t n = __ldg(poff + P);
+    if (!AFR_CHECK(n <= dc.cap, dc.derr)) n = 0;
     const uint32_t ub = (uint32_t)b;
-    // image pixel of cell pixel l (inside the image for every l that holds a record)
-    auto pixel_of = [&](uint32_t l) -> size_t {
-        return (size_t)(y0 + (int)(l / kCellW)) * (size_t)W + (size_t)(x0 + (int)(l % kCellW));
-    };
-    // cell pixel of a bucket record, kCellPix for a dead record
-    auto local_of = [&](uint32_t i, uint4 a) -> uint32_t {
-        if (i == kInvalid) return kCellPix;
-        return (uint32_t)(((int)floorf(__uint_as_float(a.y)) - y0) * kCellW + ((int)floorf(__uint_as_float(a.x)) - x0));
-    };
-    const bool multi = nc > (uint32_t)kCommitCap;
-    for (int l = tid; l < kCellPix; l += kCommitThreads) {
-        const int x = x0 + l % kCellW, y = y0 + l / kCellW;
-        sm.state[l] = (x < W && y < H) ? q.state[(size_t)y * W + x] : 0u;
-        sm.total[l] = 0;
-    }
-    __syncthreads();
-    if (multi) {
-        // per-pixel totals, to group the pixels into rounds
-        for (uint32_t j = tid; j < nc; j += kCommitThreads) {
-            const uint4 a = bk.r[(size_t)NP * (c0 + j)];
-            const uint32_t l = local_of(a.w, a);
-            if (l < kCellPix) atomicAdd(&sm.total[l], 1u);
+    const uint32_t *ridx = reinterpret_cast<const uint32_t *>(bk.r) + 3;   // batch index of record k: ridx[16 k]
+    for (uint32_t t0 = blockIdx.x * (uint32_t)kCommitTile; t0 < n; t0 += gridDim.x * (uint32_t)kCommitTile) {
+        const uint32_t e = t0 + threadIdx.x, t1 = min(t0 + (uint32_t)kCommitTile, n);
+        uint4 a = make_uint4(0u, 0u, 0u, kInvalid), q1 = a, q2 = a, q3 = a;
+        if (e < n) {
+            a = __ldg(bk.r + (size_t)NP * e);
+            q1 = __ldg(bk.r + (size_t)NP * e + 1);
+            q2 = __ldg(bk.r + (size_t)NP * e + 2);
+            if (q.world) q3 = __ldg(bk.r + (size_t)NP * e + 3);
         }
+        sidx[threadIdx.x] = a.w;
         __syncthreads();
-        // a pixel alone above one round: a warp streams the bucket
-        for (int l = warp; l < kCellPix; l += kCommitWarps) {
-            const uint32_t m = sm.total[l];
-            if (m <= (uint32_t)kCommitCap) continue;
+        // a record exists only for a valid position, so its pixel is in the image
+        const uint32_t px = e < n ? pixel_at(__uint_as_float(a.x), __uint_as_float(a.y), W) : 0u;
+        bool work = e < n && AFR_CHECK(px < P, dc.derr);
+        uint32_t beg = 0, end = 0, st = 0;
+        if (work) {
+            beg = __ldg(poff + px);
+            end = __ldg(poff + px + 1);
+            st = __ldg(state0 + px);
+            work = end - beg <= kBigPixel && (a.w != kInvalid || e == beg) && AFR_CHECK(end <= n, dc.derr);
+        }
+        if (work) {
+            // batch indices are unique; a dead record's is kInvalid, above them all
+            uint32_t rank = 0, dead = 0;
+            const uint32_t s0 = max(beg, t0), s1 = min(end, t1);
+            for (uint32_t k = beg; k < min(end, t0); ++k) {
+                const uint32_t w = __ldg(ridx + (size_t)16 * k);
+                rank += w < a.w;
+                dead += w == kInvalid;
+            }
+            for (uint32_t k = s0; k < s1; ++k) {
+                const uint32_t w = sidx[k - t0];
+                rank += w < a.w;
+                dead += w == kInvalid;
+            }
+            for (uint32_t k = max(beg, t1); k < end; ++k) {
+                const uint32_t w = __ldg(ridx + (size_t)16 * k);
+                rank += w < a.w;
+                dead += w == kInvalid;
+            }
+            const uint32_t nl = end - beg - dead;
+            if (e == beg) q.state[px] = pushed_state(st, nl, ub);
+            if (a.w != kInvalid && rank + min(nl, ub) >= nl) {   // else evicted by newer samples of the batch
+                const size_t dst = (size_t)px * ub + ((st >> 16) + rank) % ub;
+                if (AFR_CHECK(dst < q.nslots, dc.derr)) put_record<CT>(a, q1, q2, q3, dst, seq0 + a.w, q);
+            }
+        }
+        __syncthreads();   // the next tile overwrites sidx
+    }
+}
+
+// Pixels of more than kBigPixel records: a warp streams the pixel's bucket,
+// keeping the newest 32 live records by bitonic merges.
+template <int CT>
+__global__ void __launch_bounds__(256) k_pix_commit_big(const uint32_t *__restrict__ poff, uint32_t P, int b,
+                                                        uint32_t seq0, Bucket bk, Queues q,
+                                                        const uint32_t *__restrict__ state0, DebugCheck dc) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t ub = (uint32_t)b;
+    const uint32_t *ridx = reinterpret_cast<const uint32_t *>(bk.r) + 3;
+    const uint32_t n = __ldg(poff + P);
+    for (uint32_t base = warp * 32u; base < P; base += nwarps * 32u) {
+        const uint32_t p = base + (uint32_t)lane;
+        uint32_t m = 0;
+        if (p < P) m = __ldg(poff + p + 1) - __ldg(poff + p);
+        unsigned big = __ballot_sync(0xffffffffu, m > kBigPixel);
+        while (big) {
+            const uint32_t px = base + (uint32_t)(__ffs(big) - 1);
+            big &= big - 1u;
+            const uint32_t beg = __ldg(poff + px);
+            uint32_t end = __ldg(poff + px + 1);
+            if (!AFR_CHECK(end <= n && n <= dc.cap, dc.derr)) end = beg;
             unsigned long long top = 0ull;
-            for (uint32_t base = 0; base < nc; base += 32) {
-                const uint32_t j = base + (uint32_t)lane;
+            uint32_t nl = 0;
+            for (uint32_t k0 = beg; k0 < end; k0 += 32) {
+                const uint32_t k = k0 + (uint32_t)lane;
                 unsigned long long key = 0ull;
-                if (j < nc) {
-                    const uint4 a = bk.r[(size_t)NP * (c0 + j)];
-                    if (local_of(a.w, a) == (uint32_t)l) key = ((unsigned long long)(a.w + 1u) << 32) | j;
+                if (k < end) {
+                    const uint32_t w = __ldg(ridx + (size_t)16 * k);
+                    if (w != kInvalid) key = ((unsigned long long)(w + 1u) << 32) | k;
                 }
+                nl += (uint32_t)__popc(__ballot_sync(0xffffffffu, key != 0ull));
                 top = warp_top32(top, key);
             }
-            const uint32_t kept = min(m, ub);
-            uint32_t src[kPutUnroll], seq[kPutUnroll];
-#pragma unroll
-            for (int r = 0; r < kPutUnroll; ++r) src[r] = kInvalid;
-            size_t dst[kPutUnroll];
+            const uint32_t st = __ldg(state0 + px);
+            if (lane == 0) q.state[px] = pushed_state(st, nl, ub);
+            const uint32_t kept = min(nl, ub);
             if (lane >= 32 - (int)kept) {
-                const uint32_t rank = m - 32u + (uint32_t)lane;   // position in insertion order
-                src[0] = (uint32_t)top;
-                seq[0] = seq0 + (uint32_t)(top >> 32) - 1u;
-                dst[0] = pixel_of(l) * ub + ((sm.state[l] >> 16) + rank) % ub;
-            }
-            put_entries<CT, NP>(bk, c0, src, dst, seq, q, dc);
-        }
-    }
-    uint32_t group_begin = 0;
-    while (group_begin < (uint32_t)kCellPix) {
-        if (tid == 0) {
-            uint32_t e = kCellPix;
-            if (multi) {
-                uint32_t acc = 0;
-                for (e = group_begin; e < (uint32_t)kCellPix; ++e) {
-                    const uint32_t m = sm.total[e];
-                    if (m > (uint32_t)kCommitCap) continue;   // streamed above
-                    if (acc + m > (uint32_t)kCommitCap) break;
-                    acc += m;
+                const uint32_t k = (uint32_t)top, rank = nl - 32u + (uint32_t)lane;   // position in insertion order
+                const size_t dst = (size_t)px * ub + ((st >> 16) + rank) % ub;
+                if (AFR_CHECK(dst < q.nslots && k < end, dc.derr)) {
+                    const uint4 a = __ldg(bk.r + (size_t)NP * k);
+                    const uint4 q1 = __ldg(bk.r + (size_t)NP * k + 1);
+                    const uint4 q2 = __ldg(bk.r + (size_t)NP * k + 2);
+                    uint4 q3 = make_uint4(0u, 0u, 0u, 0u);
+                    if (q.world) q3 = __ldg(bk.r + (size_t)NP * k + 3);
+                    put_record<CT>(a, q1, q2, q3, dst, seq0 + a.w, q);
                 }
             }
-            sm.misc[1] = e;
-            sm.misc[0] = 0;
         }
-        for (int l = tid; l < kCellPix; l += kCommitThreads) sm.count[l] = 0;
-        __syncthreads();
-        const uint32_t ge = sm.misc[1];
-        // gather the round's records, kCommitUnroll bucket loads in flight per
-        // thread; a single round keeps record j at place j (dead ones unused)
-        for (uint32_t base = 0; base < nc; base += kCommitThreads * kCommitUnroll) {
-            uint32_t ii[kCommitUnroll];
-            uint4 aa[kCommitUnroll];
-#pragma unroll
-            for (int r = 0; r < kCommitUnroll; ++r) {
-                const uint32_t j = base + tid + r * kCommitThreads;
-                ii[r] = kInvalid;
-                if (j < nc) {
-                    aa[r] = bk.r[(size_t)NP * (c0 + j)];
-                    ii[r] = aa[r].w;
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < kCommitUnroll; ++r) {
-                const uint32_t j = base + tid + r * kCommitThreads;
-                const uint32_t l = local_of(ii[r], aa[r]);
-                // a single round marks every place: src[j] == j for a record
-                // gathered at j, kInvalid for a dead record (shared memory
-                // holds earlier blocks' values otherwise)
-                if (!multi && j < nc && l == kCellPix) sm.src[j] = kInvalid;
-                if (l < group_begin || l >= ge || (multi && sm.total[l] > (uint32_t)kCommitCap)) continue;
-                const uint32_t k = multi ? atomicAdd(&sm.misc[0], 1u) : j;
-                sm.idx[k] = ii[r];
-                sm.src[k] = j;
-                sm.lp[k] = (uint8_t)l;
-                sm.tick[k] = (uint16_t)atomicAdd(&sm.count[l], 1u);
-            }
-        }
-        __syncthreads();
-        if (warp == 0) {   // exclusive scan of the counts (128 = 4 per lane)
-            uint32_t v[4], sum = 0;
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                v[r] = sm.count[lane * 4 + r];
-                sum += v[r];
-            }
-            uint32_t incl = sum;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += t;
-            }
-            uint32_t run = incl - sum;
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                sm.start[lane * 4 + r] = run;
-                run += v[r];
-            }
-            if (lane == 31) sm.misc[0] = run;   // the round's records
-        }
-        if (!multi)
-            for (int l = tid; l < kCellPix; l += kCommitThreads) sm.total[l] = sm.count[l];
-        __syncthreads();
-        const uint32_t nr = sm.misc[0];
-        // copies of the round's records in pixel order
-        if (multi) {
-            for (uint32_t k = tid; k < nr; k += kCommitThreads) {
-                const uint32_t l = sm.lp[k], u = sm.start[l] + sm.tick[k];
-                sm.sidx[u] = sm.idx[k];
-                sm.ssrc[u] = sm.src[k];
-                sm.slp[u] = (uint8_t)l;
-            }
-        } else {
-            for (uint32_t j = tid; j < nc; j += kCommitThreads) {
-                if (sm.src[j] != j) continue;   // a dead record's place
-                const uint32_t l = sm.lp[j], u = sm.start[l] + sm.tick[j];
-                sm.sidx[u] = sm.idx[j];
-                sm.ssrc[u] = j;
-                sm.slp[u] = (uint8_t)l;
-            }
-        }
-        __syncthreads();
-        // up to 32 records in a pixel: a thread per record counts the pixel's
-        // records with a smaller batch index (batch indices are unique)
-        for (uint32_t u0 = 0; u0 < nr; u0 += kCommitThreads * kPutUnroll) {
-            uint32_t src[kPutUnroll], seq[kPutUnroll];
-            size_t dst[kPutUnroll];
-#pragma unroll
-            for (int r = 0; r < kPutUnroll; ++r) {
-                const uint32_t u = u0 + tid + r * kCommitThreads;
-                src[r] = kInvalid;
-                if (u >= nr) continue;
-                const uint32_t l = sm.slp[u], m = sm.count[l];
-                if (m > 32u) continue;
-                const uint32_t beg = sm.start[l], me = sm.sidx[u];
-                uint32_t rank = 0;
-                for (uint32_t v = beg; v < beg + m; ++v) rank += sm.sidx[v] < me;
-                if (rank + min(m, ub) < m) continue;   // evicted by newer samples of the batch
-                src[r] = sm.ssrc[u];
-                seq[r] = seq0 + me;
-                dst[r] = pixel_of(l) * ub + ((sm.state[l] >> 16) + rank) % ub;
-            }
-            put_entries<CT, NP>(bk, c0, src, dst, seq, q, dc);
-        }
-        // more than 32: a warp keeps the newest 32 by bitonic merges of the
-        // pixel's records, 32 at a time
-        for (uint32_t l = group_begin + (uint32_t)warp; l < ge; l += kCommitWarps) {
-            const uint32_t m = sm.count[l];
-            if (m <= 32u) continue;
-            const uint32_t beg = sm.start[l];
-            unsigned long long top = 0ull;
-            for (uint32_t base = 0; base < m; base += 32) {
-                unsigned long long key = 0ull;
-                if (base + (uint32_t)lane < m) {
-                    const uint32_t u = beg + base + lane;
-                    key = ((unsigned long long)(sm.sidx[u] + 1u) << 32) | u;
-                }
-                top = warp_top32(top, key);
-            }
-            const uint32_t kept = min(m, ub);
-            uint32_t src[kPutUnroll], seq[kPutUnroll];
-#pragma unroll
-            for (int r = 0; r < kPutUnroll; ++r) src[r] = kInvalid;
-            size_t dst[kPutUnroll];
-            if (lane >= 32 - (int)kept) {
-                const uint32_t u = (uint32_t)top, rank = m - 32u + (uint32_t)lane;
-                src[0] = sm.ssrc[u];
-                seq[0] = seq0 + sm.sidx[u];
-                dst[0] = pixel_of(l) * ub + ((sm.state[l] >> 16) + rank) % ub;
-            }
-            put_entries<CT, NP>(bk, c0, src, dst, seq, q, dc);
-        }
-        __syncthreads();
-        group_begin = ge;
-    }
-    // queue states after pushing each pixel's records
-    for (int l = tid; l < kCellPix; l += kCommitThreads) {
-        const uint32_t m = sm.total[l];
-        if (m == 0) continue;
-        const uint32_t st = sm.state[l], cnt = st & 0xFFFFu, h = st >> 16;
-        const uint32_t cn = (uint64_t)cnt + m < (uint64_t)ub ? cnt + m : ub;
-        const uint32_t hn = (uint32_t)((h + (uint64_t)m) % ub);
-        q.state[pixel_of((uint32_t)l)] = cn | (hn << 16);
     }
 }
 
 template <int CT>
 cudaError_t run(AfrContext *c, const float4 *pos, const void *col, const float2 *mo, const float4 *world, uint32_t n,
                 uint32_t seq0, cudaStream_t s) {
-    const int ncx = (c->W + kCellW - 1) / kCellW;
-    const int nkeys = c->ncells * kSubBuckets;
+    const uint32_t P = (uint32_t)c->P;
     const DebugCheck dc{(uint32_t)c->batch_cap, c->derr};
     Bucket bk{c->bucket};
-    static bool attr_set = false;   // per colour type: raise the commit kernels' shared-memory limit once
-    cudaError_t e = cudaSuccess;
-    if (!attr_set) {
-        e = cudaFuncSetAttribute(k_cell_commit<CT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kCommitSmemBytes);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    if ((e = cudaMemsetAsync(c->ccnt, 0, sizeof(uint32_t) * nkeys, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(c->ccur, 0, sizeof(uint32_t) * nkeys, s)) != cudaSuccess) return e;
-    const int g = grid_for(n, 256);
-    k_cell_count<<<g, 256, 0, s>>>(pos, n, c->W, c->H, ncx, c->ccnt);
-    if ((e = scan_exclusive(c->ccnt, c->coff, nkeys, c->scan_tmp, s)) != cudaSuccess) return e;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(c->ccnt, 0, sizeof(uint32_t) * P, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->ccur, 0, sizeof(uint32_t) * P, s)) != cudaSuccess) return e;
+    k_pix_count<<<grid_for(n, 256), 256, 0, s>>>(pos, n, c->W, c->H, c->ccnt);
+    if ((e = scan_exclusive(c->ccnt, c->coff, P, c->scan_tmp, s)) != cudaSuccess) return e;
     const int gs = grid_for((n + kScatterUnroll - 1) / kScatterUnroll, 32 * kScatterWarps);
     uint32_t *accept = c->fifo_n ? c->fifo_flag : nullptr;
+    k_pix_scatter<CT><<<gs, 32 * kScatterWarps, 0, s>>>(pos, col, mo, c->r_world ? world : nullptr, n, c->W, c->H,
+                                                        c->coff, c->ccur, bk, accept, c->dcount, dc);
+    // the cursors are spent: they take the queue states before the batch,
+    // which every commit thread reads
+    if ((e = cudaMemcpyAsync(c->ccur, c->r_state, sizeof(uint32_t) * P, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return e;
     Queues q{c->r_xy, c->r_mo, c->r_t, c->r_depth, c->r_seq, c->r_col, c->r_state, c->r_world, c->nslots};
-    k_cell_scatter<CT, 4><<<gs, 32 * kScatterWarps, 0, s>>>(pos, col, mo, c->r_world ? world : nullptr, n, c->W, c->H,
-                                                             ncx, c->coff, c->ccur, bk, accept, c->dcount, dc);
-    k_cell_commit<CT, 4><<<c->ncells, kCommitThreads, kCommitSmemBytes, s>>>(c->coff, c->W, c->H, ncx, c->b, seq0, bk,
-                                                                             q, dc);
+    k_pix_commit<CT><<<grid_for(n, kCommitTile), kCommitTile, 0, s>>>(c->coff, P, c->W, c->b, seq0, bk, q, c->ccur,
+                                                                      dc);
+    k_pix_commit_big<CT><<<grid_for(P, 256), 256, 0, s>>>(c->coff, P, c->b, seq0, bk, q, c->ccur, dc);
     return cudaGetLastError();
 }
 
 }  // namespace
-
-int ingest_sub_buckets() { return kSubBuckets; }
 
 namespace {
 

@@ -4,9 +4,8 @@
 //
 //  count:  thread per queue slot; x' = x + m_x (t_now - t) with one rounding
 //          per operation (__fmul_rn / __fadd_rn, so no contraction), drops
-//          samples leaving the image, counts per destination bin (warp-
-//          aggregated) and keeps the smallest a^2 per bin (the filter's
-//          exponent shift).
+//          samples leaving the image and counts per destination bin (the
+//          lanes of a warp grouped by bin with one match instruction).
 //  scan:   bin offsets.
 //  list:   same slot walk; each moved sample writes its slot index and its
 //          sequence number into its bin's lists (unordered, 8 bytes a sample).
@@ -18,6 +17,8 @@
 //          mostly share a bin, so the rank scans are broadcast reads and the
 //          record writes cover whole sectors; the frame view, and every sum
 //          over it, is deterministic without a reorder pass over the records.
+//          Each bin's smallest a^2 (the filter's exponent shift) is the
+//          minimum over the bin's warp segments, one atomic each.
 #include "afr_internal.cuh"
 
 namespace afr {
@@ -84,72 +85,61 @@ __device__ __forceinline__ bool slot_live(uint32_t st, int s, int b) {
 }
 
 // FIFO: the slots are the reconstructor queue's, live below min(*state, nslots)
-// (state then points at its count of accepted samples).
+// (state then points at its count of accepted samples). The slot's data is
+// loaded together with its pixel's state (one round trip, not two).
+template <bool FIFO, bool CAM>
+__device__ __forceinline__ bool live_move(uint32_t i, uint32_t nlive, int b, int bshift, int W, int H, float t_now,
+                                          const Camera &cam, const float4 *__restrict__ world,
+                                          const uint32_t *__restrict__ state, const float2 *__restrict__ r_xy,
+                                          const float2 *__restrict__ r_mo, const float *__restrict__ r_t, Moved &mv,
+                                          bool &live) {
+    uint32_t p = 0, st = 0;
+    int s = 0;
+    live = false;
+    if (FIFO) {
+        if (i >= nlive) return false;
+    } else {
+        split_slot(i, b, bshift, p, s);
+        st = __ldg(state + p);
+    }
+    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 xy = make_float2(0.f, 0.f);
+    if (CAM) w = __ldg(world + i);
+    else xy = __ldg(r_xy + i);
+    const float2 m = __ldg(r_mo + i);
+    const float t = __ldg(r_t + i);
+    if (!FIFO && !slot_live(st, s, b)) return false;
+    live = true;
+    mv = CAM ? move_camera(w, m, t, t_now, W, H, cam) : move_sample(xy, m, t, t_now, W, H);
+    return mv.ok;
+}
+
 template <bool FIFO, bool CAM>
 __global__ void __launch_bounds__(256) k_count(uint32_t nslots, int b, int bshift, int W, int H, float t_now,
                                                Camera cam, const float4 *__restrict__ world,
                                                const uint32_t *__restrict__ state, const float2 *__restrict__ r_xy,
                                                const float2 *__restrict__ r_mo, const float *__restrict__ r_t,
-                                               uint32_t *__restrict__ fcnt, uint32_t *__restrict__ amin2,
-                                               unsigned long long *__restrict__ dcount) {
+                                               uint32_t *__restrict__ fcnt, unsigned long long *__restrict__ dcount) {
     const uint32_t nlive = FIFO ? min(__ldg(state), nslots) : 0u;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nslots; i += gridDim.x * blockDim.x) {
-        if (FIFO) {
-            if (i >= nlive) continue;
-        } else {
-            uint32_t p;
-            int s;
-            split_slot(i, b, bshift, p, s);
-            if (!slot_live(__ldg(state + p), s, b)) continue;
-        }
-        Moved mv = CAM ? move_camera(__ldg(world + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H, cam)
-                       : move_sample(__ldg(r_xy + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H);
-        agg_count(dcount + CNT_DROPPED, !mv.ok);
-        if (!mv.ok) continue;
-        // lanes sharing a bin add their count and their smallest a^2 through
-        // the lowest of them (a^2 >= 0: bit order = value order); after
-        // kGroupRounds bins the remaining lanes add their own
-        const unsigned active = __activemask();
-        const int lane = threadIdx.x & 31;
-        const uint32_t a2bits = __float_as_uint(mv.a2);
-        unsigned todo = active;
-        for (int round = 0; round < kGroupRounds && todo; ++round) {
-            const int leader = __ffs(todo) - 1;
-            const uint32_t k = __shfl_sync(active, mv.bin, leader);
-            const bool in = mv.bin == k;
-            const unsigned peers = __ballot_sync(active, in);
-            const uint32_t bits = __reduce_min_sync(active, in ? a2bits : 0xFFFFFFFFu);
-            if (lane == leader) {
-                atomicAdd(fcnt + k, (uint32_t)__popc(peers));
-                atomicMin(amin2 + k, bits);
-            }
-            todo &= ~peers;
-        }
-        if (todo & (1u << lane)) {
-            atomicAdd(fcnt + mv.bin, 1u);
-            atomicMin(amin2 + mv.bin, a2bits);
-        }
+    const int lane = threadIdx.x & 31;
+    uint32_t dropped = 0;
+    // warp-uniform trip count: every lane of a warp reaches the match below
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < nslots; i0 += stride) {
+        const uint32_t i = i0 + (uint32_t)lane;
+        Moved mv;
+        mv.ok = false;
+        bool live = false;
+        if (i < nslots)
+            live_move<FIFO, CAM>(i, nlive, b, bshift, W, H, t_now, cam, world, state, r_xy, r_mo, r_t, mv, live);
+        dropped += live && !mv.ok;
+        // lanes sharing a bin add their count through the lowest of them
+        const uint32_t key = mv.ok ? mv.bin : kInvalid;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (mv.ok && lane == __ffs(peers) - 1) atomicAdd(fcnt + mv.bin, (uint32_t)__popc(peers));
     }
-}
-
-// The slot walk shared by the list and place passes: the moved sample of
-// live slot i, or !ok.
-template <bool FIFO, bool CAM>
-__device__ __forceinline__ bool live_move(uint32_t i, uint32_t nlive, int b, int bshift, int W, int H, float t_now,
-                                          const Camera &cam, const float4 *__restrict__ world,
-                                          const uint32_t *__restrict__ state, const float2 *__restrict__ r_xy,
-                                          const float2 *__restrict__ r_mo, const float *__restrict__ r_t, Moved &mv) {
-    if (FIFO) {
-        if (i >= nlive) return false;
-    } else {
-        uint32_t p;
-        int s;
-        split_slot(i, b, bshift, p, s);
-        if (!slot_live(__ldg(state + p), s, b)) return false;
-    }
-    mv = CAM ? move_camera(__ldg(world + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H, cam)
-             : move_sample(__ldg(r_xy + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H);
-    return mv.ok;
+    const uint32_t d = __reduce_add_sync(0xffffffffu, dropped);
+    if (lane == 0 && d) atomicAdd(dcount + CNT_DROPPED, (unsigned long long)d);
 }
 
 template <bool FIFO, bool CAM>
@@ -161,19 +151,39 @@ __global__ void __launch_bounds__(256) k_list(uint32_t nslots, int b, int bshift
                                               uint32_t *__restrict__ fcur, uint32_t *__restrict__ flist,
                                               uint32_t *__restrict__ flseq, DebugCheck dc) {
     const uint32_t nlive = FIFO ? min(__ldg(state), nslots) : 0u;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nslots; i += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < nslots; i0 += stride) {
+        const uint32_t i = i0 + (uint32_t)lane;
         Moved mv;
-        if (!live_move<FIFO, CAM>(i, nlive, b, bshift, W, H, t_now, cam, world, state, r_xy, r_mo, r_t, mv)) continue;
-        const uint32_t at = __ldg(foff + mv.bin) + agg_inc(fcur, mv.bin);
+        mv.ok = false;
+        uint32_t sq = 0;
+        bool live = false;
+        if (i < nslots) {
+            sq = __ldg(r_seq + i);
+            live_move<FIFO, CAM>(i, nlive, b, bshift, W, H, t_now, cam, world, state, r_xy, r_mo, r_t, mv, live);
+        }
+        // lanes sharing a bin take one ticket atomic through the lowest of them
+        const uint32_t key = mv.ok ? mv.bin : kInvalid;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (!mv.ok) continue;
+        const int leader = __ffs(peers) - 1;
+        uint32_t first = 0;
+        const uint32_t off = __ldg(foff + mv.bin);
+        if (lane == leader) first = atomicAdd(fcur + mv.bin, (uint32_t)__popc(peers));
+        const uint32_t at = off + __shfl_sync(peers, first, leader) + __popc(peers & ((1u << lane) - 1u));
         if (AFR_CHECK(at < dc.cap, dc.derr)) {
             flist[at] = i;
-            flseq[at] = __ldg(r_seq + i);
+            flseq[at] = sq;
         }
     }
 }
 
 // fcnt holds every bin's count here; a bin above kSortedBinMax records takes
 // its ranks by counting fcnt down (arrival order) and is counted as unsorted.
+// The frame records arrive in bin order, so the lanes of a warp that share a
+// bin are one segment: its smallest a^2 goes to amin2 with one atomic (the
+// filter's exponent shift; bit order = value order for a^2 >= 0).
 template <int CT, bool FIFO, bool CAM>
 __global__ void __launch_bounds__(256) k_place(int W, int H, float t_now, Camera cam, const float4 *__restrict__ world,
                                                const float2 *__restrict__ r_xy, const float2 *__restrict__ r_mo,
@@ -181,17 +191,34 @@ __global__ void __launch_bounds__(256) k_place(int W, int H, float t_now, Camera
                                                const void *__restrict__ r_col, uint32_t P,
                                                const uint32_t *__restrict__ foff, const uint32_t *__restrict__ flist,
                                                const uint32_t *__restrict__ flseq, uint32_t *__restrict__ fcnt,
-                                               float4 *__restrict__ fpos,
+                                               uint32_t *__restrict__ amin2, float4 *__restrict__ fpos,
                                                void *__restrict__ fcol, uint32_t *__restrict__ fseq,
                                                unsigned long long *__restrict__ dcount, DebugCheck dc, uint32_t nsrc) {
     using CS = ColorStore<CT>;
     uint32_t n = __ldg(foff + P);
     if (!AFR_CHECK(n <= dc.cap, dc.derr)) n = 0;
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        const uint32_t i = __ldg(flist + e);
-        if (!AFR_CHECK(i < nsrc, dc.derr)) continue;
-        const Moved mv = CAM ? move_camera(__ldg(world + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H, cam)
-                             : move_sample(__ldg(r_xy + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H);
+    const int lane = threadIdx.x & 31;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    // warp-uniform trip count: every lane of a warp reaches the match below
+    for (uint32_t e0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); e0 < n; e0 += stride) {
+        const uint32_t e = e0 + (uint32_t)lane;
+        uint32_t i = 0;
+        bool ok = e < n;
+        if (ok) {
+            i = __ldg(flist + e);
+            ok = AFR_CHECK(i < nsrc, dc.derr);
+        }
+        Moved mv;
+        mv.ok = false;
+        mv.bin = kInvalid;
+        if (ok)
+            mv = CAM ? move_camera(__ldg(world + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H, cam)
+                     : move_sample(__ldg(r_xy + i), __ldg(r_mo + i), __ldg(r_t + i), t_now, W, H);
+        const uint32_t key = mv.ok ? mv.bin : kInvalid;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (!mv.ok) continue;
+        const uint32_t bits = __reduce_min_sync(peers, __float_as_uint(mv.a2));
+        if (lane == __ffs(peers) - 1) atomicMin(amin2 + mv.bin, bits);
         const uint32_t sq = __ldg(flseq + e);
         const uint32_t beg = __ldg(foff + mv.bin), end = __ldg(foff + mv.bin + 1);
         uint32_t rank = 0;
@@ -237,7 +264,7 @@ cudaError_t launch_reproject(AfrContext *c, float t_now, const Camera *camp, cud
     const DebugCheck dc{(uint32_t)c->frame_cap, c->derr};
 #define AFR_COUNT(F_, C_)                                                                                    \
     k_count<F_, C_><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, cm, wp, state, xy, mo, tt, c->fcnt, \
-                                      c->amin2, c->dcount)
+                                      c->dcount)
     if (fifo && cam) AFR_COUNT(true, true);
     else if (fifo) AFR_COUNT(true, false);
     else if (cam) AFR_COUNT(false, true);
@@ -255,7 +282,8 @@ cudaError_t launch_reproject(AfrContext *c, float t_now, const Camera *camp, cud
 #undef AFR_LIST
 #define AFR_PLACE(CT_, F_, C_)                                                                                     \
     k_place<CT_, F_, C_><<<g, 256, 0, s>>>(c->W, c->H, t_now, cm, wp, xy, mo, tt, sq, col, (uint32_t)c->P, c->foff, \
-                                           c->flist, c->flseq, c->fcnt, c->fpos, c->fcol, c->fseq, c->dcount, dc, ns)
+                                           c->flist, c->flseq, c->fcnt, c->amin2, c->fpos, c->fcol, c->fseq,       \
+                                           c->dcount, dc, ns)
 #define AFR_REPROJ(CT_)                                                                                        \
     do {                                                                                                       \
         if (fifo && cam) AFR_PLACE(CT_, true, true);                                                           \

@@ -148,3 +148,23 @@ def test_batch_refresh_matches_calls_in_series(dev, streams):
     assert all(r.status() == L.AFR_OK for r in recs)
     B.close()
 
+
+
+@pytest.mark.parametrize("beta_s,want_r", [(2.5, 4), (3.2, 5)])
+def test_autotuner_wider_radii(dev, beta_s, want_r):
+    """Wider spatial widths (sigma_s = beta_s everywhere) make the tuner take
+    R = 4 and R = 5, and the batched call at that radius still equals the
+    single-stream launches bit for bit."""
+    from paper_2510_15876_gb300 import autotune
+    from paper_2510_15876_gb300.api import BatchReconstructor
+    prm = (0.0, beta_s, 4.0, 1.0, 0.0, 1.0)
+    recs, _ = _make(dev)
+    tuned = [autotune.tune(r, T_NOW, prm) for r in recs]
+    assert all(t[0] == want_r for t in tuned), tuned
+    singles = [r.reconstruct(T_NOW, prm).clone() for r in recs]
+    B = BatchReconstructor(recs)
+    outs = B.run(T_NOW, prm)
+    torch.cuda.synchronize()
+    for a, b in zip(singles, outs):
+        assert torch.equal(a, b)
+    B.close()

@@ -120,11 +120,12 @@ def test_ingest_bitexact(dev, W, H, b, n, batches):
 
 
 @pytest.mark.parametrize("W,H,b,dense,spread,batches", [(16, 8, 4, 0, 10000, 2), (40, 20, 8, 8000, 3000, 2),
-                                                        (37, 19, 32, 0, 60000, 1)])
-def test_ingest_dense_cells_bitexact(dev, W, H, b, dense, spread, batches):
-    """Batches denser than one commit round of a 16 x 8 cell (more than 3072
-    records in a cell: rounds over groups of pixels) and a single pixel with
-    more than a round on its own (ranked by a warp streaming the bucket), over
+                                                        (37, 19, 32, 0, 60000, 1), (10, 7, 16, 0, 50000, 2)])
+def test_ingest_dense_tiles_bitexact(dev, W, H, b, dense, spread, batches):
+    """Dense batches: tens of records a pixel (ranked by a thread per record,
+    with pixels crossing the commit's shared-memory tiles), one pixel with
+    8,000 records and every pixel of a 10 x 7 image above 256 records (a warp
+    streams the pixel's bucket keeping its newest 32), rejected samples, over
     consecutive batches, bit for bit against the oracle's queues."""
     rng = np.random.default_rng(W + H + b)
     rec = _mk(dev, W, H, b)

@@ -70,6 +70,9 @@ CONFIGS: dict[str, SceneSpec] = {
     # 1920x1080, 16-deep, 256 moving discs, ~10% of pixels on occlusion edges
     "c3_1920x1080x16": SceneSpec("c3_1920x1080x16", 1920, 1080, 16, 256, (8.0, 24.0), 64.0, 16,
                                  edge_fraction=0.10),
+    # a quarter of the 1920x1080x16 scene (same sample, disc and edge densities),
+    # for counter captures that must stay a few GB on the device
+    "p3_960x540x16": SceneSpec("p3_960x540x16", 960, 540, 16, 64, (8.0, 24.0), 64.0, 16, edge_fraction=0.10),
     # 512x512, 8-deep, 32 moving discs (differentiation form)
     "c4_512x512x8": SceneSpec("c4_512x512x8", 512, 512, 8, 32, (12.0, 40.0), 32.0, 16),
 }
