@@ -7,8 +7,9 @@
 //          samples leaving the image and counts per destination bin (the
 //          lanes of a warp grouped by bin with one match instruction).
 //  scan:   bin offsets.
-//  list:   same slot walk; each moved sample writes its slot index and its
-//          sequence number into its bin's lists (unordered, 8 bytes a sample).
+//  list:   each moved sample (its bin kept by the count pass, 4 bytes a
+//          slot) writes its slot index and its sequence number into its bin's
+//          lists (unordered, 8 bytes a sample).
 //  place:  thread per frame record, in bin order: the slot of list entry e
 //          is moved again, its rank in the bin is the number of sequence
 //          numbers in the bin's list below its own (sequence numbers are
@@ -114,67 +115,89 @@ __device__ __forceinline__ bool live_move(uint32_t i, uint32_t nlive, int b, int
     return mv.ok;
 }
 
+// A warp takes kCountRows rows of 32 slots at a time, their loads issued
+// together.
+constexpr int kCountRows = 4;
 template <bool FIFO, bool CAM>
 __global__ void __launch_bounds__(256) k_count(uint32_t nslots, int b, int bshift, int W, int H, float t_now,
                                                Camera cam, const float4 *__restrict__ world,
                                                const uint32_t *__restrict__ state, const float2 *__restrict__ r_xy,
                                                const float2 *__restrict__ r_mo, const float *__restrict__ r_t,
-                                               uint32_t *__restrict__ fcnt, unsigned long long *__restrict__ dcount) {
+                                               uint32_t *__restrict__ fcnt, uint32_t *__restrict__ sbin,
+                                               unsigned long long *__restrict__ dcount) {
     const uint32_t nlive = FIFO ? min(__ldg(state), nslots) : 0u;
     const int lane = threadIdx.x & 31;
     uint32_t dropped = 0;
-    // warp-uniform trip count: every lane of a warp reaches the match below
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < nslots; i0 += stride) {
-        const uint32_t i = i0 + (uint32_t)lane;
-        Moved mv;
-        mv.ok = false;
-        bool live = false;
-        if (i < nslots)
-            live_move<FIFO, CAM>(i, nlive, b, bshift, W, H, t_now, cam, world, state, r_xy, r_mo, r_t, mv, live);
-        dropped += live && !mv.ok;
-        // lanes sharing a bin add their count through the lowest of them
-        const uint32_t key = mv.ok ? mv.bin : kInvalid;
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        if (mv.ok && lane == __ffs(peers) - 1) atomicAdd(fcnt + mv.bin, (uint32_t)__popc(peers));
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i0 = warp * 32u * kCountRows; i0 < nslots; i0 += nwarps * 32u * kCountRows) {
+        Moved mv[kCountRows];
+        bool live[kCountRows];
+#pragma unroll
+        for (int r = 0; r < kCountRows; ++r) {
+            const uint32_t i = i0 + (uint32_t)(r * 32 + lane);
+            mv[r].ok = false;
+            live[r] = false;
+            if (i < nslots)
+                live_move<FIFO, CAM>(i, nlive, b, bshift, W, H, t_now, cam, world, state, r_xy, r_mo, r_t, mv[r],
+                                     live[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < kCountRows; ++r) {
+            const uint32_t i = i0 + (uint32_t)(r * 32 + lane);
+            dropped += live[r] && !mv[r].ok;
+            const uint32_t key = mv[r].ok ? mv[r].bin : kInvalid;
+            if (i < nslots) sbin[i] = key;
+            const unsigned peers = __match_any_sync(0xffffffffu, key);
+            if (mv[r].ok && lane == __ffs(peers) - 1) atomicAdd(fcnt + mv[r].bin, (uint32_t)__popc(peers));
+        }
     }
     const uint32_t d = __reduce_add_sync(0xffffffffu, dropped);
     if (lane == 0 && d) atomicAdd(dcount + CNT_DROPPED, (unsigned long long)d);
 }
 
-template <bool FIFO, bool CAM>
-__global__ void __launch_bounds__(256) k_list(uint32_t nslots, int b, int bshift, int W, int H, float t_now,
-                                              Camera cam, const float4 *__restrict__ world,
-                                              const uint32_t *__restrict__ state, const float2 *__restrict__ r_xy,
-                                              const float2 *__restrict__ r_mo, const float *__restrict__ r_t,
+// The slots' bins from the count pass (kInvalid: dead or moved out). A warp
+// takes kListRows rows of 32 slots at a time and issues every row's ticket
+// atomic before it reads any back, so the atomics' latencies overlap.
+constexpr int kListRows = 8;
+__global__ void __launch_bounds__(256) k_list(uint32_t nslots, const uint32_t *__restrict__ sbin,
                                               const uint32_t *__restrict__ r_seq, const uint32_t *__restrict__ foff,
                                               uint32_t *__restrict__ fcur, uint32_t *__restrict__ flist,
                                               uint32_t *__restrict__ flseq, DebugCheck dc) {
-    const uint32_t nlive = FIFO ? min(__ldg(state), nslots) : 0u;
     const int lane = threadIdx.x & 31;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < nslots; i0 += stride) {
-        const uint32_t i = i0 + (uint32_t)lane;
-        Moved mv;
-        mv.ok = false;
-        uint32_t sq = 0;
-        bool live = false;
-        if (i < nslots) {
-            sq = __ldg(r_seq + i);
-            live_move<FIFO, CAM>(i, nlive, b, bshift, W, H, t_now, cam, world, state, r_xy, r_mo, r_t, mv, live);
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i0 = warp * 32u * kListRows; i0 < nslots; i0 += nwarps * 32u * kListRows) {
+        uint32_t bin[kListRows], sq[kListRows], off[kListRows], first[kListRows];
+        unsigned peers[kListRows];
+#pragma unroll
+        for (int r = 0; r < kListRows; ++r) {
+            const uint32_t i = i0 + (uint32_t)(r * 32 + lane);
+            bin[r] = kInvalid;
+            sq[r] = 0;
+            if (i < nslots) {
+                bin[r] = __ldg(sbin + i);
+                sq[r] = __ldg(r_seq + i);
+            }
         }
-        // lanes sharing a bin take one ticket atomic through the lowest of them
-        const uint32_t key = mv.ok ? mv.bin : kInvalid;
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        if (!mv.ok) continue;
-        const int leader = __ffs(peers) - 1;
-        uint32_t first = 0;
-        const uint32_t off = __ldg(foff + mv.bin);
-        if (lane == leader) first = atomicAdd(fcur + mv.bin, (uint32_t)__popc(peers));
-        const uint32_t at = off + __shfl_sync(peers, first, leader) + __popc(peers & ((1u << lane) - 1u));
-        if (AFR_CHECK(at < dc.cap, dc.derr)) {
-            flist[at] = i;
-            flseq[at] = sq;
+#pragma unroll
+        for (int r = 0; r < kListRows; ++r) {
+            peers[r] = __match_any_sync(0xffffffffu, bin[r]);
+            first[r] = 0;
+            off[r] = 0;
+            if (bin[r] != kInvalid) {
+                off[r] = __ldg(foff + bin[r]);
+                if (lane == __ffs(peers[r]) - 1) first[r] = atomicAdd(fcur + bin[r], (uint32_t)__popc(peers[r]));
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kListRows; ++r) {
+            const uint32_t i = i0 + (uint32_t)(r * 32 + lane);
+            const uint32_t f = __shfl_sync(0xffffffffu, first[r], bin[r] != kInvalid ? __ffs(peers[r]) - 1 : lane);
+            if (bin[r] == kInvalid) continue;
+            const uint32_t at = off[r] + f + __popc(peers[r] & ((1u << lane) - 1u));
+            if (AFR_CHECK(at < dc.cap, dc.derr)) {
+                flist[at] = i;
+                flseq[at] = sq[r];
+            }
         }
     }
 }
@@ -264,7 +287,7 @@ cudaError_t launch_reproject(AfrContext *c, float t_now, const Camera *camp, cud
     const DebugCheck dc{(uint32_t)c->frame_cap, c->derr};
 #define AFR_COUNT(F_, C_)                                                                                    \
     k_count<F_, C_><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, cm, wp, state, xy, mo, tt, c->fcnt, \
-                                      c->dcount)
+                                      c->fseq, c->dcount)
     if (fifo && cam) AFR_COUNT(true, true);
     else if (fifo) AFR_COUNT(true, false);
     else if (cam) AFR_COUNT(false, true);
@@ -272,14 +295,8 @@ cudaError_t launch_reproject(AfrContext *c, float t_now, const Camera *camp, cud
 #undef AFR_COUNT
     if ((e = scan_exclusive(c->fcnt, c->foff, c->P, c->scan_tmp, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->fcnt, 0, sizeof(uint32_t) * c->P, s)) != cudaSuccess) return e;
-#define AFR_LIST(F_, C_)                                                                                       \
-    k_list<F_, C_><<<g, 256, 0, s>>>(ns, c->b, bshift, c->W, c->H, t_now, cm, wp, state, xy, mo, tt, sq, c->foff, \
-                                     c->fcnt, c->flist, c->flseq, dc)
-    if (fifo && cam) AFR_LIST(true, true);
-    else if (fifo) AFR_LIST(true, false);
-    else if (cam) AFR_LIST(false, true);
-    else AFR_LIST(false, false);
-#undef AFR_LIST
+    // fseq holds each slot's bin until the placement pass writes the frame
+    k_list<<<g, 256, 0, s>>>(ns, c->fseq, sq, c->foff, c->fcnt, c->flist, c->flseq, dc);
 #define AFR_PLACE(CT_, F_, C_)                                                                                     \
     k_place<CT_, F_, C_><<<g, 256, 0, s>>>(c->W, c->H, t_now, cm, wp, xy, mo, tt, sq, col, (uint32_t)c->P, c->foff, \
                                            c->flist, c->flseq, c->fcnt, c->amin2, c->fpos, c->fcol, c->fseq,       \
