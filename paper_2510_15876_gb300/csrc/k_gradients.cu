@@ -1,6 +1,6 @@
 // k_gradients.cu -- sections 4 and 4.1 on the deep buffer.
 //
-//  pixel pass   (a group of lanes per pixel, one per queue slot): age
+//  pixel pass   (a group of lanes per pixel, several queue slots each): age
 //               weights exp(-3.47 a), weighted mean luminance and its weighted
 //               spread (per-pixel moments for the tile variance), and the
 //               temporal gradient over the queue sorted by time.
@@ -12,15 +12,40 @@
 namespace afr {
 namespace {
 
-// Group of G lanes (G = queue depth rounded up to a power of two) per pixel:
-// lane k of the group holds the pixel's k-th newest sample, so the loads of a
-// warp are contiguous; sums, the time sort and the pairwise differences use
-// shuffles within the group.
-template <int G>
+// Group of L = G / S lanes per pixel (G = queue depth rounded up to a power
+// of two), S queue entries per lane: entry k (0 the newest) sits in lane
+// k mod L, register k / L, so the loads of a warp stay contiguous per pixel and
+// a warp serves 32 S / G pixels; sums, the time sort and the pairwise
+// differences use shuffles within the group.
+template <int L>
 __device__ __forceinline__ float group_sum(float v) {
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
+    for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, L);
     return v;
+}
+
+// The value of entry k + 1 for each of a lane's entries k = r L + l.
+template <int L, int S, typename V>
+__device__ __forceinline__ void next_entry(const V (&v)[S], V (&nv)[S], int l) {
+#pragma unroll
+    for (int r = 0; r < S; ++r) {
+        const V d = __shfl_down_sync(0xffffffffu, v[r], 1, L);
+        if (r + 1 < S) {
+            const V w = __shfl_sync(0xffffffffu, v[r + 1], 0, L);   // entry (r + 1) L follows entry r L + L - 1
+            nv[r] = l == L - 1 ? w : d;
+        } else {
+            nv[r] = d;
+        }
+    }
+}
+
+struct Entry {
+    float T, w, cx, cy, cz;
+    uint32_t Q;
+};
+
+__device__ __forceinline__ bool newer(const Entry &a, const Entry &b) {   // descending order by (T, Q)
+    return (a.T > b.T) || (a.T == b.T && a.Q > b.Q);
 }
 
 // Luminance differences carry the gradients: the spatial gradient is a
@@ -34,83 +59,153 @@ __device__ __forceinline__ float group_sum(float v) {
 // temporal gradient takes each consecutive pair's difference from its colour
 // differences; the age weights, the time steps and the variance moments are
 // FP32.
-template <int CT, int G>
+template <int CT, int G, int S>
 __global__ void __launch_bounds__(256) k_pixel(int P, int b, float t_now, const uint32_t *__restrict__ state,
                                                const float *__restrict__ r_t, const uint32_t *__restrict__ r_seq,
                                                const void *__restrict__ r_col, float2 *__restrict__ lbar,
                                                float4 *__restrict__ pstat) {
     using CS = ColorStore<CT>;
-    const int k = threadIdx.x & (G - 1);
-    const int groups = (gridDim.x * blockDim.x) / G;
+    constexpr int L = G / S;
+    const int l = threadIdx.x & (L - 1);
+    const int groups = (gridDim.x * blockDim.x) / L;
     // every lane of a warp runs the same number of iterations (P rounded up)
-    const int P_round = (P + (32 / G) - 1) / (32 / G) * (32 / G);
-    for (int p = (blockIdx.x * blockDim.x + threadIdx.x) / G; p < P_round; p += groups) {
+    const int P_round = (P + (32 / L) - 1) / (32 / L) * (32 / L);
+    for (int p = (blockIdx.x * blockDim.x + threadIdx.x) / L; p < P_round; p += groups) {
         const bool pix = p < P;
-        uint32_t st = pix ? __ldg(state + p) : 0u;
-        int n = (int)(st & 0xFFFFu), h = (int)(st >> 16);
-        bool valid = k < n;
-        float T = -INFINITY, w = 0.f;
-        float3 c = make_float3(0.f, 0.f, 0.f);
-        uint32_t Q = 0;
-        if (valid) {
-            int s = h - 1 - k;
-            if (s < 0) s += b;
-            size_t i = (size_t)p * b + s;
-            T = __ldg(r_t + i);
-            Q = __ldg(r_seq + i);
-            c = CS::load(r_col, i);
-            w = expf(-kAgeDecay * fmaxf(t_now - T, 0.f));
+        const uint32_t st = pix ? __ldg(state + p) : 0u;
+        const int n = (int)(st & 0xFFFFu), h = (int)(st >> 16);
+        Entry E[S];
+        float D[S];
+#pragma unroll
+        for (int r = 0; r < S; ++r) {
+            const int k = r * L + l;
+            E[r] = Entry{-INFINITY, 0.f, 0.f, 0.f, 0.f, 0u};
+            if (k < n) {
+                int s = h - 1 - k;
+                if (s < 0) s += b;
+                const size_t i = (size_t)p * b + s;
+                E[r].T = __ldg(r_t + i);
+                E[r].Q = __ldg(r_seq + i);
+                const float3 c = CS::load(r_col, i);
+                E[r].cx = c.x;
+                E[r].cy = c.y;
+                E[r].cz = c.z;
+            }
         }
-        // reference: the newest sample (lane 0 of the group)
-        const float3 cr = make_float3(__shfl_sync(0xffffffffu, c.x, 0, G), __shfl_sync(0xffffffffu, c.y, 0, G),
-                                      __shfl_sync(0xffffffffu, c.z, 0, G));
-        float D = 0.f;   // L - L_r
-        if (valid) D = fmaf(kLumB, __fsub_rn(c.z, cr.z), fmaf(kLumG, __fsub_rn(c.y, cr.y), kLumR * __fsub_rn(c.x, cr.x)));
-        const float sw = group_sum<G>(w);
-        const float swd = group_sum<G>(w * D);
+#pragma unroll
+        for (int r = 0; r < S; ++r)
+            if (r * L + l < n) E[r].w = expf(-kAgeDecay * fmaxf(t_now - E[r].T, 0.f));
+        // reference: the newest sample (entry 0: lane 0, register 0)
+        const float3 cr = make_float3(__shfl_sync(0xffffffffu, E[0].cx, 0, L),
+                                      __shfl_sync(0xffffffffu, E[0].cy, 0, L),
+                                      __shfl_sync(0xffffffffu, E[0].cz, 0, L));
+        float lw = 0.f, lwd = 0.f;
+#pragma unroll
+        for (int r = 0; r < S; ++r) {   // L - L_r
+            D[r] = r * L + l < n ? fmaf(kLumB, __fsub_rn(E[r].cz, cr.z),
+                                        fmaf(kLumG, __fsub_rn(E[r].cy, cr.y), kLumR * __fsub_rn(E[r].cx, cr.x)))
+                                 : 0.f;
+            lw += E[r].w;
+            lwd += E[r].w * D[r];
+        }
+        const float sw = group_sum<L>(lw);
+        const float swd = group_sum<L>(lwd);
         const float delta = n > 0 ? swd / sw : 0.f;   // mean - L_r
-        const float dd = valid ? D - delta : 0.f;
-        const float m2 = group_sum<G>(w * dd * dd);
+        float lm2 = 0.f;
+#pragma unroll
+        for (int r = 0; r < S; ++r) {
+            const float dd = r * L + l < n ? D[r] - delta : 0.f;
+            lm2 += E[r].w * dd * dd;
+        }
+        const float m2 = group_sum<L>(lm2);
         // newest first by time, equal times newest first by sequence number;
         // queues filled in time order are already in that order
-        float Tn = __shfl_down_sync(0xffffffffu, T, 1, G);
-        uint32_t Qn = __shfl_down_sync(0xffffffffu, Q, 1, G);
-        bool ordered = !(k + 1 < n) || (T > Tn) || (T == Tn && Q > Qn);
+        float T[S], Tn[S];
+        uint32_t Q[S], Qn[S];
+#pragma unroll
+        for (int r = 0; r < S; ++r) {
+            T[r] = E[r].T;
+            Q[r] = E[r].Q;
+        }
+        next_entry<L, S>(T, Tn, l);
+        next_entry<L, S>(Q, Qn, l);
+        bool ordered = true;
+#pragma unroll
+        for (int r = 0; r < S; ++r)
+            ordered = ordered && (!(r * L + l + 1 < n) || (T[r] > Tn[r]) || (T[r] == Tn[r] && Q[r] > Qn[r]));
         if (!__all_sync(0xffffffffu, ordered)) {
-            // bitonic sort of the group descending by (T, Q); empty lanes (-inf) sink
+            // bitonic sort of the group's G entries descending by (T, Q);
+            // empty entries (-inf) sink. Entry e = r L + l: the partner at
+            // distance j < L is in lane l ^ j, at j >= L in register r ^ (j / L)
+            // of the same lane.
 #pragma unroll
             for (int kk = 2; kk <= G; kk <<= 1) {
 #pragma unroll
                 for (int j = kk >> 1; j > 0; j >>= 1) {
-                    float To = __shfl_xor_sync(0xffffffffu, T, j, G);
-                    uint32_t Qo = __shfl_xor_sync(0xffffffffu, Q, j, G);
-                    float cxo = __shfl_xor_sync(0xffffffffu, c.x, j, G);
-                    float cyo = __shfl_xor_sync(0xffffffffu, c.y, j, G);
-                    float czo = __shfl_xor_sync(0xffffffffu, c.z, j, G);
-                    float wo = __shfl_xor_sync(0xffffffffu, w, j, G);
-                    bool mine_first = (T > To) || (T == To && Q > Qo);   // descending order
-                    bool lower = (k & j) == 0, desc = (k & kk) == 0;
-                    bool keep = (lower == desc) ? mine_first : !mine_first;
-                    if (!keep) { T = To; Q = Qo; c = make_float3(cxo, cyo, czo); w = wo; }
+                    if (j >= L) {
+#pragma unroll
+                        for (int r = 0; r < S; ++r) {
+                            const int r2 = r ^ (j / L);
+                            if (r2 < r) continue;   // each pair once, from its lower entry
+                            const bool desc = ((r * L + l) & kk) == 0;
+                            if (newer(E[r], E[r2]) != desc) {
+                                const Entry t = E[r];
+                                E[r] = E[r2];
+                                E[r2] = t;
+                            }
+                        }
+                        continue;
+                    }
+#pragma unroll
+                    for (int r = 0; r < S; ++r) {
+                        const int e = r * L + l;
+                        Entry o;
+                        o.T = __shfl_xor_sync(0xffffffffu, E[r].T, j, L);
+                        o.Q = __shfl_xor_sync(0xffffffffu, E[r].Q, j, L);
+                        o.cx = __shfl_xor_sync(0xffffffffu, E[r].cx, j, L);
+                        o.cy = __shfl_xor_sync(0xffffffffu, E[r].cy, j, L);
+                        o.cz = __shfl_xor_sync(0xffffffffu, E[r].cz, j, L);
+                        o.w = __shfl_xor_sync(0xffffffffu, E[r].w, j, L);
+                        const bool lower = (e & j) == 0, desc = (e & kk) == 0;
+                        const bool keep = (lower == desc) ? newer(E[r], o) : !newer(E[r], o);
+                        if (!keep) E[r] = o;
+                    }
                 }
             }
         }
         // consecutive luminance differences from the colour differences
-        const float3 cn = make_float3(__shfl_down_sync(0xffffffffu, c.x, 1, G), __shfl_down_sync(0xffffffffu, c.y, 1, G),
-                                      __shfl_down_sync(0xffffffffu, c.z, 1, G));
-        Tn = __shfl_down_sync(0xffffffffu, T, 1, G);
-        bool pair = k + 1 < n;
-        const float dL = fmaf(kLumB, __fsub_rn(c.z, cn.z), fmaf(kLumG, __fsub_rn(c.y, cn.y), kLumR * __fsub_rn(c.x, cn.x)));
-        float num = group_sum<G>(pair ? w * fabsf(dL) : 0.f);
-        float den = group_sum<G>(pair ? w * (T - Tn) : 0.f);
-        if (k == 0 && pix) {
+        float cx[S], cy[S], cz[S], cxn[S], cyn[S], czn[S];
+#pragma unroll
+        for (int r = 0; r < S; ++r) {
+            T[r] = E[r].T;
+            cx[r] = E[r].cx;
+            cy[r] = E[r].cy;
+            cz[r] = E[r].cz;
+        }
+        next_entry<L, S>(cx, cxn, l);
+        next_entry<L, S>(cy, cyn, l);
+        next_entry<L, S>(cz, czn, l);
+        next_entry<L, S>(T, Tn, l);
+        float num = 0.f, den = 0.f;
+#pragma unroll
+        for (int r = 0; r < S; ++r) {
+            if (r * L + l + 1 < n) {
+                const float dL = fmaf(kLumB, __fsub_rn(cz[r], czn[r]),
+                                      fmaf(kLumG, __fsub_rn(cy[r], cyn[r]), kLumR * __fsub_rn(cx[r], cxn[r])));
+                num += E[r].w * fabsf(dL);
+                den += E[r].w * (T[r] - Tn[r]);
+            }
+        }
+        num = group_sum<L>(num);
+        den = group_sum<L>(den);
+        if (l == 0 && pix) {
             if (n == 0) {
                 lbar[p] = make_float2(__int_as_float(0x7fc00000), 0.f);
                 pstat[p] = make_float4(0.f, 0.f, 0.f, 0.f);
             } else {
                 const dfloat Lr = luminance_df(cr);
                 const dfloat mean = df_add(Lr, {delta, 0.f});
-                float gt = (n >= 2 && den > 0.f) ? num / den : 0.f;
+                const float gt = (n >= 2 && den > 0.f) ? num / den : 0.f;
                 lbar[p] = make_float2(mean.h, mean.l);
                 pstat[p] = make_float4(sw, mean.h, m2, gt);
             }
@@ -225,17 +320,25 @@ __global__ void __launch_bounds__(kTileThreads) k_spatial_tiles(int W, int H, in
     }
 }
 
+// Queue entries per lane of the pixel pass.
+constexpr int kPixelEntries = 2;
+
 template <int CT>
 cudaError_t launch_pixel(AfrContext *c, float t_now, cudaStream_t s) {
+    constexpr int S = kPixelEntries;
     int g = grid_for((size_t)c->P * 32, 256, 16 * device_sms());
     if (c->b <= 4)
-        k_pixel<CT, 4><<<g, 256, 0, s>>>(c->P, c->b, t_now, c->r_state, c->r_t, c->r_seq, c->r_col, c->lbar, c->pstat);
+        k_pixel<CT, 4, 2><<<g, 256, 0, s>>>(c->P, c->b, t_now, c->r_state, c->r_t, c->r_seq, c->r_col, c->lbar,
+                                            c->pstat);
     else if (c->b <= 8)
-        k_pixel<CT, 8><<<g, 256, 0, s>>>(c->P, c->b, t_now, c->r_state, c->r_t, c->r_seq, c->r_col, c->lbar, c->pstat);
+        k_pixel<CT, 8, S><<<g, 256, 0, s>>>(c->P, c->b, t_now, c->r_state, c->r_t, c->r_seq, c->r_col, c->lbar,
+                                            c->pstat);
     else if (c->b <= 16)
-        k_pixel<CT, 16><<<g, 256, 0, s>>>(c->P, c->b, t_now, c->r_state, c->r_t, c->r_seq, c->r_col, c->lbar, c->pstat);
+        k_pixel<CT, 16, S><<<g, 256, 0, s>>>(c->P, c->b, t_now, c->r_state, c->r_t, c->r_seq, c->r_col, c->lbar,
+                                             c->pstat);
     else
-        k_pixel<CT, 32><<<g, 256, 0, s>>>(c->P, c->b, t_now, c->r_state, c->r_t, c->r_seq, c->r_col, c->lbar, c->pstat);
+        k_pixel<CT, 32, S><<<g, 256, 0, s>>>(c->P, c->b, t_now, c->r_state, c->r_t, c->r_seq, c->r_col, c->lbar,
+                                             c->pstat);
     return cudaGetLastError();
 }
 
