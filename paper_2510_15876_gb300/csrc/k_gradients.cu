@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(kTileThreads) k_spatial_tiles(int W, int H, in
 }
 
 // Queue entries per lane of the pixel pass.
-constexpr int kPixelEntries = 2;
+constexpr int kPixelEntries = 4;
 
 template <int CT>
 cudaError_t launch_pixel(AfrContext *c, float t_now, cudaStream_t s) {
