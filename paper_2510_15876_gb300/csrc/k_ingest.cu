@@ -86,8 +86,7 @@ constexpr int kScatterUnroll = 2;   // samples (and ticket atomics) in flight pe
 template <int CT>
 __global__ void __launch_bounds__(32 * kScatterWarps) k_pix_scatter(
     const float4 *__restrict__ pos, const void *__restrict__ col, const float2 *__restrict__ mo,
-    const float4 *__restrict__ world, uint32_t n, int W, int H, const uint32_t *__restrict__ poff,
-    uint32_t *__restrict__ pcur, Bucket bk, uint32_t *__restrict__ accept, unsigned long long *__restrict__ dcount,
+    const float4 *__restrict__ world, uint32_t n, int W, int H, uint32_t *__restrict__ pcur, Bucket bk, uint32_t *__restrict__ accept, unsigned long long *__restrict__ dcount,
     DebugCheck dc) {
     using CS = ColorStore<CT>;
     __shared__ uint4 stage[kScatterWarps][32][5];   // 80-byte stride: conflict-free 16-byte accesses
@@ -121,7 +120,7 @@ __global__ void __launch_bounds__(32 * kScatterWarps) k_pix_scatter(
             d[r] = kInvalid;
             if (pok) {
                 const uint32_t px = pixel_at(p[r].x, p[r].y, W);
-                d[r] = __ldg(poff + px) + atomicAdd(pcur + px, 1u);
+                d[r] = atomicAdd(pcur + px, 1u);   // the cursors start at the bucket offsets
                 if (!AFR_CHECK(d[r] < dc.cap, dc.derr)) d[r] = kInvalid;
             }
         }
@@ -355,13 +354,15 @@ cudaError_t run(AfrContext *c, const float4 *pos, const void *col, const float2 
     Bucket bk{c->bucket};
     cudaError_t e;
     if ((e = cudaMemsetAsync(c->ccnt, 0, sizeof(uint32_t) * P, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(c->ccur, 0, sizeof(uint32_t) * P, s)) != cudaSuccess) return e;
     k_pix_count<<<grid_for(n, 256), 256, 0, s>>>(pos, n, c->W, c->H, c->ccnt);
     if ((e = scan_exclusive(c->ccnt, c->coff, P, c->scan_tmp, s)) != cudaSuccess) return e;
+    // append cursors start at the bucket offsets: a ticket is the record's place
+    if ((e = cudaMemcpyAsync(c->ccur, c->coff, sizeof(uint32_t) * P, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return e;
     const int gs = grid_for((n + kScatterUnroll - 1) / kScatterUnroll, 32 * kScatterWarps);
     uint32_t *accept = c->fifo_n ? c->fifo_flag : nullptr;
     k_pix_scatter<CT><<<gs, 32 * kScatterWarps, 0, s>>>(pos, col, mo, c->r_world ? world : nullptr, n, c->W, c->H,
-                                                        c->coff, c->ccur, bk, accept, c->dcount, dc);
+                                                        c->ccur, bk, accept, c->dcount, dc);
     // the cursors are spent: they take the queue states before the batch,
     // which every commit thread reads
     if ((e = cudaMemcpyAsync(c->ccur, c->r_state, sizeof(uint32_t) * P, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)

@@ -160,13 +160,12 @@ __global__ void __launch_bounds__(256) k_count(uint32_t nslots, int b, int bshif
 // atomic before it reads any back, so the atomics' latencies overlap.
 constexpr int kListRows = 8;
 __global__ void __launch_bounds__(256) k_list(uint32_t nslots, const uint32_t *__restrict__ sbin,
-                                              const uint32_t *__restrict__ r_seq, const uint32_t *__restrict__ foff,
-                                              uint32_t *__restrict__ fcur, uint32_t *__restrict__ flist,
+                                              const uint32_t *__restrict__ r_seq, uint32_t *__restrict__ fcur, uint32_t *__restrict__ flist,
                                               uint32_t *__restrict__ flseq, DebugCheck dc) {
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t i0 = warp * 32u * kListRows; i0 < nslots; i0 += nwarps * 32u * kListRows) {
-        uint32_t bin[kListRows], sq[kListRows], off[kListRows], first[kListRows];
+        uint32_t bin[kListRows], sq[kListRows], first[kListRows];
         unsigned peers[kListRows];
 #pragma unroll
         for (int r = 0; r < kListRows; ++r) {
@@ -182,18 +181,15 @@ __global__ void __launch_bounds__(256) k_list(uint32_t nslots, const uint32_t *_
         for (int r = 0; r < kListRows; ++r) {
             peers[r] = __match_any_sync(0xffffffffu, bin[r]);
             first[r] = 0;
-            off[r] = 0;
-            if (bin[r] != kInvalid) {
-                off[r] = __ldg(foff + bin[r]);
-                if (lane == __ffs(peers[r]) - 1) first[r] = atomicAdd(fcur + bin[r], (uint32_t)__popc(peers[r]));
-            }
+            if (bin[r] != kInvalid && lane == __ffs(peers[r]) - 1)
+                first[r] = atomicAdd(fcur + bin[r], (uint32_t)__popc(peers[r]));
         }
 #pragma unroll
         for (int r = 0; r < kListRows; ++r) {
             const uint32_t i = i0 + (uint32_t)(r * 32 + lane);
             const uint32_t f = __shfl_sync(0xffffffffu, first[r], bin[r] != kInvalid ? __ffs(peers[r]) - 1 : lane);
             if (bin[r] == kInvalid) continue;
-            const uint32_t at = off[r] + f + __popc(peers[r] & ((1u << lane) - 1u));
+            const uint32_t at = f + __popc(peers[r] & ((1u << lane) - 1u));
             if (AFR_CHECK(at < dc.cap, dc.derr)) {
                 flist[at] = i;
                 flseq[at] = sq[r];
@@ -202,8 +198,9 @@ __global__ void __launch_bounds__(256) k_list(uint32_t nslots, const uint32_t *_
     }
 }
 
-// fcnt holds every bin's count here; a bin above kSortedBinMax records takes
-// its ranks by counting fcnt down (arrival order) and is counted as unsorted.
+// fcnt holds every bin's end here (the list's cursors); a bin above
+// kSortedBinMax records takes its ranks by counting it down (arrival order)
+// and is counted as unsorted.
 // The frame records arrive in bin order, so the lanes of a warp that share a
 // bin are one segment: its smallest a^2 goes to amin2 with one atomic (the
 // filter's exponent shift; bit order = value order for a^2 >= 0).
@@ -248,7 +245,7 @@ __global__ void __launch_bounds__(256) k_place(int W, int H, float t_now, Camera
         if (end - beg <= (uint32_t)kSortedBinMax) {
             for (uint32_t k = beg; k < end; ++k) rank += __ldg(flseq + k) < sq;
         } else {
-            rank = atomicSub(fcnt + mv.bin, 1u) - 1u;
+            rank = atomicSub(fcnt + mv.bin, 1u) - 1u - beg;   // the cursor ends at the bin's end
             if (rank == 0) atomicAdd(dcount + CNT_UNSORTED, 1ull);
         }
         const uint32_t d = beg + rank;
@@ -294,9 +291,11 @@ cudaError_t launch_reproject(AfrContext *c, float t_now, const Camera *camp, cud
     else AFR_COUNT(false, false);
 #undef AFR_COUNT
     if ((e = scan_exclusive(c->fcnt, c->foff, c->P, c->scan_tmp, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(c->fcnt, 0, sizeof(uint32_t) * c->P, s)) != cudaSuccess) return e;
+    // the list's append cursors start at the bin offsets (a ticket is the entry's place)
+    if ((e = cudaMemcpyAsync(c->fcnt, c->foff, sizeof(uint32_t) * c->P, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return e;
     // fseq holds each slot's bin until the placement pass writes the frame
-    k_list<<<g, 256, 0, s>>>(ns, c->fseq, sq, c->foff, c->fcnt, c->flist, c->flseq, dc);
+    k_list<<<g, 256, 0, s>>>(ns, c->fseq, sq, c->fcnt, c->flist, c->flseq, dc);
 #define AFR_PLACE(CT_, F_, C_)                                                                                     \
     k_place<CT_, F_, C_><<<g, 256, 0, s>>>(c->W, c->H, t_now, cm, wp, xy, mo, tt, sq, col, (uint32_t)c->P, c->foff, \
                                            c->flist, c->flseq, c->fcnt, c->amin2, c->fpos, c->fcol, c->fseq,       \
