@@ -86,8 +86,8 @@ constexpr int kScatterUnroll = 2;   // samples (and ticket atomics) in flight pe
 template <int CT>
 __global__ void __launch_bounds__(32 * kScatterWarps) k_pix_scatter(
     const float4 *__restrict__ pos, const void *__restrict__ col, const float2 *__restrict__ mo,
-    const float4 *__restrict__ world, uint32_t n, int W, int H, uint32_t *__restrict__ pcur, Bucket bk, uint32_t *__restrict__ accept, unsigned long long *__restrict__ dcount,
-    DebugCheck dc) {
+    const float4 *__restrict__ world, uint32_t n, int W, int H, uint32_t *__restrict__ pcur, Bucket bk,
+    uint32_t *__restrict__ accept, unsigned long long *__restrict__ dcount, DebugCheck dc) {
     using CS = ColorStore<CT>;
     __shared__ uint4 stage[kScatterWarps][32][5];   // 80-byte stride: conflict-free 16-byte accesses
     __shared__ uint32_t dest[kScatterWarps][32];
