@@ -229,10 +229,12 @@ def run_ours(args, rank, world):
         r.refresh(T_NOW, out=out, tiles=tiles)
 
     class Pipelined:
-        """The timed steps: step k + 1's reset and insert run on an ingest
-        stream as soon as step k's gradients and reprojection are done with
-        the sample buffers, beside step k's filter (which reads none of
-        them); every step still does all of a1-a6."""
+        """The timed steps: step k + 1's insert runs on an ingest stream. Its
+        binning (counting, offsets, bucket records: the context's scratch)
+        starts at once, beside step k's gradients and reprojection; its reset
+        and commit wait until those are done with the sample buffers
+        (afr_insert_samples_ex with reads_done) and run beside step k's
+        filter, which reads none of them. Every step still does all of a1-a6."""
 
         def __init__(self, r):
             self.r = r
@@ -242,11 +244,9 @@ def run_ours(args, rank, world):
 
         def step(self, pos, col, mo, out, tiles, ready=None, consumed=None):
             main = torch.cuda.current_stream()
-            self.ingest.wait_event(self.reads_done)
             if ready is not None:
                 self.ingest.wait_event(ready)
-            self.r.reset(stream=self.ingest)
-            self.r.insert(pos, col, mo, stream=self.ingest)
+            self.r.insert(pos, col, mo, stream=self.ingest, reset=True, queues_free=self.reads_done)
             if consumed is not None:
                 consumed.record(self.ingest)
             self.ingested.record(self.ingest)

@@ -55,6 +55,8 @@ extern "C" {
 
 /* Same type as the CUDA runtime's cudaStream_t; 0 is the legacy stream. */
 typedef struct CUstream_st *afr_stream_t;
+/* Same type as the CUDA runtime's cudaEvent_t. */
+typedef struct CUevent_st *afr_event_t;
 
 typedef enum {
     AFR_OK = 0,
@@ -160,6 +162,26 @@ AFR_API AfrStatus afr_reserve(AfrContext *ctx, uint32_t n);
  * Invalidates gradients and the frame view. n = 0 is a no-op. */
 AFR_API AfrStatus afr_insert_samples(AfrContext *ctx, const AfrSampleBatch *batch, uint32_t n,
                              afr_stream_t stream);
+
+/* afr_insert_samples (section 4) with two options for pipelined image loops.
+ *   flags        AFR_INSERT_RESET: the queues, the reconstructor queue and the
+ *                counters are cleared before the batch enters them, as
+ *                afr_reset followed by afr_insert_samples would do (the
+ *                batch's sequence numbers start at 0).
+ *   queues_free  a CUDA event (cudaEvent_t) or NULL. The steps that read or
+ *                write the queues (the reset, the copy of the queue states,
+ *                the commit, the reconstructor-queue append) first wait for
+ *                it on the stream; the binning before them (counting, bucket
+ *                offsets, the 64-byte bucket records: scratch of this
+ *                context) does not. Recorded when the previous image's
+ *                afr_estimate_gradients and afr_reproject are done with the
+ *                queues, it lets the next batch's binning run beside them.
+ *                The event must have been recorded when the call is made.
+ * The result equals afr_insert_samples (after afr_reset with the flag) bit
+ * for bit. Errors as afr_insert_samples; unknown flags: AFR_ERR_INVALID_ARG. */
+#define AFR_INSERT_RESET 1u
+AFR_API AfrStatus afr_insert_samples_ex(AfrContext *ctx, const AfrSampleBatch *batch, uint32_t n, uint32_t flags,
+                                        afr_event_t queues_free, afr_stream_t stream);
 
 /* Sections 4 and 4.1: per-pixel age-weighted mean luminance (weights
  * exp(-3.47 a), a = max(0, t_now - t)), spatial gradients G_x, G_y (mean of

@@ -16,6 +16,7 @@ DEBUG_LIB_PATH = os.path.join(_PKG, "libafr_debug.so")   # AFR_DEBUG build: devi
 c_i32, c_u32, c_u64, c_f32, c_p = ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_float, ctypes.c_void_p
 
 AFR_OK, AFR_ERR_INVALID_ARG, AFR_ERR_BAD_STATE, AFR_ERR_OOM, AFR_ERR_CUDA, AFR_ERR_TIMEOUT, AFR_ERR_DEVICE_CHECK = range(7)
+AFR_INSERT_RESET = 1
 STATUS_NAMES = ["AFR_OK", "AFR_ERR_INVALID_ARG", "AFR_ERR_BAD_STATE", "AFR_ERR_OOM", "AFR_ERR_CUDA",
                 "AFR_ERR_TIMEOUT", "AFR_ERR_DEVICE_CHECK"]
 AFR_F32, AFR_F16, AFR_BF16 = 0, 1, 2
@@ -31,7 +32,7 @@ EXPORTED = [
     "afr_export_map", "afr_import_map", "afr_set_frame_colors", "afr_reproject_batch_static", "afr_set_tuning",
     "afr_profile_filter", "afr_profile_read", "afr_tile_error", "afr_reproject_camera",
     "afr_batch_create", "afr_batch_destroy", "afr_batch_reconstruct", "afr_measure_alu_peaks",
-    "afr_batch_refresh",
+    "afr_batch_refresh", "afr_insert_samples_ex",
 ]
 
 
@@ -74,6 +75,7 @@ def _declare(L):
         "afr_reset": (S, [c_p, c_p]),
         "afr_reserve": (S, [c_p, c_u32]),
         "afr_insert_samples": (S, [c_p, ctypes.POINTER(AfrSampleBatch), c_u32, c_p]),
+        "afr_insert_samples_ex": (S, [c_p, ctypes.POINTER(AfrSampleBatch), c_u32, c_u32, c_p, c_p]),
         "afr_estimate_gradients": (S, [c_p, c_f32, c_p]),
         "afr_reproject": (S, [c_p, c_f32, c_p]),
         "afr_reconstruct": (S, [c_p, c_f32, ctypes.POINTER(AfrParams), c_p, c_p]),

@@ -98,8 +98,11 @@ class Reconstructor:
         self._check(self.lib.afr_reserve(self.h, n))
 
     def insert(self, pos: torch.Tensor, color: torch.Tensor, motion: torch.Tensor, world: torch.Tensor | None = None,
-               stream=None):
-        """world: [n, 4] float32 hit points (X, Y, Z, -) for world_points contexts."""
+               stream=None, reset: bool = False, queues_free=None):
+        """world: [n, 4] float32 hit points (X, Y, Z, -) for world_points contexts.
+        reset: clear the queues first (as reset() then insert()). queues_free
+        (a recorded torch.cuda.Event): the steps that touch the queues wait
+        for it, the binning before them does not (afr_insert_samples_ex)."""
         n = pos.shape[0]
         arrays = [(pos, torch.float32, 4), (color, self.color_dtype, 4), (motion, torch.float32, 2)]
         if world is not None:
@@ -109,7 +112,12 @@ class Reconstructor:
                 raise ValueError(f"batch tensor must be contiguous {dt} [{n}, {cols}] on {self.device}")
         batch = L.AfrSampleBatch(pos.data_ptr(), color.data_ptr(), motion.data_ptr(),
                                  None if world is None else world.data_ptr())
-        self._check(self.lib.afr_insert_samples(self.h, ctypes.byref(batch), n, _stream(stream)))
+        if not reset and queues_free is None:
+            self._check(self.lib.afr_insert_samples(self.h, ctypes.byref(batch), n, _stream(stream)))
+            return
+        ev = None if queues_free is None else ctypes.c_void_p(queues_free.cuda_event)
+        self._check(self.lib.afr_insert_samples_ex(self.h, ctypes.byref(batch), n,
+                                                   L.AFR_INSERT_RESET if reset else 0, ev, _stream(stream)))
 
     def estimate_gradients(self, t_now: float = 1.0, stream=None):
         self._check(self.lib.afr_estimate_gradients(self.h, t_now, _stream(stream)))

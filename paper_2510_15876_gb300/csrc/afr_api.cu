@@ -60,7 +60,7 @@ cudaError_t dalloc(T **p, size_t n) {
 void free_all(AfrContext *c) {
     void *ptrs[] = {c->r_xy, c->r_mo, c->r_t, c->r_depth, c->r_seq, c->r_col, c->r_state, c->bucket, c->fifo_flag, c->fifo_rank, c->fifo_scan,
                     c->ccnt, c->coff, c->ccur, c->lbar, c->grad, c->pstat, c->sigma, c->tile_terms, c->fconst, c->cov_r[0], c->cov_r[1], c->cov_n, c->amin2, c->tiles, c->fcnt,
-                    c->foff, c->fpos, c->fcol, c->fseq, c->flist, c->flseq, c->q_xy, c->q_mo, c->q_t, c->q_seq, c->q_col, c->q_total, c->q_world, c->r_world, c->scan_tmp, c->bgrad, c->bparam, c->dcount, c->derr};
+                    c->foff, c->fpos, c->fcol, c->fseq, c->flist, c->flseq, c->q_xy, c->q_mo, c->q_t, c->q_seq, c->q_col, c->q_total, c->q_world, c->r_world, c->scan_tmp, c->scan_tmp_in, c->bgrad, c->bparam, c->dcount, c->derr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -237,6 +237,7 @@ AfrStatus afr_create(const AfrConfig *cfg, AfrContext **out) {
     AFR_ALLOC(c->flist, c->frame_cap);
     AFR_ALLOC(c->flseq, c->frame_cap);
     AFR_ALLOC(c->scan_tmp, c->scan_tmp_n);
+    AFR_ALLOC(c->scan_tmp_in, c->scan_tmp_n);
     AFR_ALLOC(c->bgrad, 2 * P);
     AFR_ALLOC(c->bparam, (size_t)c->n_bblocks * 6);
     AFR_ALLOC(c->dcount, (size_t)afr::CNT_N);
@@ -317,27 +318,49 @@ AfrStatus afr_reserve(AfrContext *c, uint32_t n) {
     return AFR_OK;
 }
 
-AfrStatus afr_insert_samples(AfrContext *c, const AfrSampleBatch *batch, uint32_t n, afr_stream_t stream) {
-    Range nvtx_range("afr_insert_samples");
+static AfrStatus insert_impl(AfrContext *c, const AfrSampleBatch *batch, uint32_t n, uint32_t flags,
+                             cudaEvent_t queues_free, cudaStream_t s) {
     if (!c) return AFR_ERR_INVALID_ARG;
-    if (n == 0) return AFR_OK;
+    if (flags & ~(uint32_t)AFR_INSERT_RESET) return fail(c, AFR_ERR_INVALID_ARG, "afr_insert_samples_ex: unknown flag");
+    const bool reset = (flags & AFR_INSERT_RESET) != 0;
+    if (n == 0) {
+        if (!reset) return AFR_OK;
+        if (queues_free) {
+            const cudaError_t e = cudaStreamWaitEvent(s, queues_free, 0);
+            if (e != cudaSuccess) return cuda_fail(c, e, "afr_insert_samples_ex");
+        }
+        return afr_reset(c, reinterpret_cast<afr_stream_t>(s));
+    }
     if (!batch || !batch->pos_dev || !batch->color_dev || !batch->motion_dev)
         return fail(c, AFR_ERR_INVALID_ARG, "afr_insert_samples: null batch pointer");
     if (!aligned(batch->pos_dev, 16) || !aligned(batch->color_dev, c->csize) || !aligned(batch->motion_dev, 8))
         return fail(c, AFR_ERR_INVALID_ARG, "afr_insert_samples: misaligned batch array");
     if (c->r_world && (!batch->world_dev || !aligned(batch->world_dev, 16)))
         return fail(c, AFR_ERR_INVALID_ARG, "afr_insert_samples: this context needs 16-byte aligned world points");
-    if (c->inserted + n > 0xFFFFFFFFull)
+    const uint64_t seq0 = reset ? 0 : c->inserted;
+    if (seq0 + n > 0xFFFFFFFFull)
         return fail(c, AFR_ERR_INVALID_ARG, "afr_insert_samples: sequence numbers exhausted; call afr_reset");
     AfrStatus st = afr_reserve(c, n);
     if (st != AFR_OK) return st;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    cudaError_t e = afr::launch_ingest(c, batch, n, (uint32_t)c->inserted, s);
-    if (e == cudaSuccess && c->fifo_n) e = afr::launch_fifo_append(c, batch, n, (uint32_t)c->inserted, s);
+    cudaError_t e = afr::launch_ingest(c, batch, n, (uint32_t)seq0, s, queues_free, reset);
+    if (e == cudaSuccess && c->fifo_n) e = afr::launch_fifo_append(c, batch, n, (uint32_t)seq0, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "afr_insert_samples");
-    c->inserted += n;
+    if (reset) c->err.clear();
+    c->inserted = seq0 + n;
     c->grads_valid = c->frame_valid = c->recon_valid = false;
     return AFR_OK;
+}
+
+AfrStatus afr_insert_samples(AfrContext *c, const AfrSampleBatch *batch, uint32_t n, afr_stream_t stream) {
+    Range nvtx_range("afr_insert_samples");
+    return insert_impl(c, batch, n, 0u, nullptr, reinterpret_cast<cudaStream_t>(stream));
+}
+
+AfrStatus afr_insert_samples_ex(AfrContext *c, const AfrSampleBatch *batch, uint32_t n, uint32_t flags,
+                                afr_event_t queues_free, afr_stream_t stream) {
+    Range nvtx_range("afr_insert_samples_ex");
+    return insert_impl(c, batch, n, flags, reinterpret_cast<cudaEvent_t>(queues_free),
+                       reinterpret_cast<cudaStream_t>(stream));
 }
 
 AfrStatus afr_estimate_gradients(AfrContext *c, float t_now, afr_stream_t stream) {

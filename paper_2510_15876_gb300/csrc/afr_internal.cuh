@@ -150,7 +150,8 @@ struct AfrContext {
     size_t frame_cap = 0;
 
     // scan scratch
-    uint32_t *scan_tmp = nullptr;
+    uint32_t *scan_tmp = nullptr;       // scan block sums of the reprojection
+    uint32_t *scan_tmp_in = nullptr;    // ... of the ingest (it may run beside the reprojection)
     size_t scan_tmp_n = 0;
 
     // backward scratch
@@ -341,8 +342,11 @@ inline int grid_for(size_t n, int block, int cap = 0) {
 cudaError_t scan_exclusive(const uint32_t *in, uint32_t *out, size_t n, uint32_t *tmp, cudaStream_t s);
 size_t scan_tmp_elems(size_t n);
 
+// queues_free: the steps that touch the queues wait for it (may be null);
+// reset: the queues, the reconstructor queue and the counters are cleared
+// before the commit (the rejected count at the start).
 cudaError_t launch_ingest(AfrContext *c, const AfrSampleBatch *batch, uint32_t n, uint32_t seq0,
-                          cudaStream_t s);
+                          cudaStream_t s, cudaEvent_t queues_free = nullptr, bool reset = false);
 cudaError_t launch_fifo_append(AfrContext *c, const AfrSampleBatch *batch, uint32_t n, uint32_t seq0, cudaStream_t s);
 cudaError_t launch_gradients(AfrContext *c, float t_now, cudaStream_t s);
 cudaError_t launch_reproject(AfrContext *c, float t_now, const Camera *cam, cudaStream_t s);

@@ -348,14 +348,17 @@ __global__ void __launch_bounds__(256) k_pix_commit_big(const uint32_t *__restri
 
 template <int CT>
 cudaError_t run(AfrContext *c, const float4 *pos, const void *col, const float2 *mo, const float4 *world, uint32_t n,
-                uint32_t seq0, cudaStream_t s) {
+                uint32_t seq0, cudaStream_t s, cudaEvent_t queues_free, bool reset) {
     const uint32_t P = (uint32_t)c->P;
     const DebugCheck dc{(uint32_t)c->batch_cap, c->derr};
     Bucket bk{c->bucket};
     cudaError_t e;
+    // binning: the context's scratch only (the scatter counts the rejected samples)
+    if (reset && (e = cudaMemsetAsync(c->dcount + CNT_REJECTED, 0, sizeof(unsigned long long), s)) != cudaSuccess)
+        return e;
     if ((e = cudaMemsetAsync(c->ccnt, 0, sizeof(uint32_t) * P, s)) != cudaSuccess) return e;
     k_pix_count<<<grid_for(n, 256), 256, 0, s>>>(pos, n, c->W, c->H, c->ccnt);
-    if ((e = scan_exclusive(c->ccnt, c->coff, P, c->scan_tmp, s)) != cudaSuccess) return e;
+    if ((e = scan_exclusive(c->ccnt, c->coff, P, c->scan_tmp_in, s)) != cudaSuccess) return e;
     // append cursors start at the bucket offsets: a ticket is the record's place
     if ((e = cudaMemcpyAsync(c->ccur, c->coff, sizeof(uint32_t) * P, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return e;
@@ -363,6 +366,15 @@ cudaError_t run(AfrContext *c, const float4 *pos, const void *col, const float2 
     uint32_t *accept = c->fifo_n ? c->fifo_flag : nullptr;
     k_pix_scatter<CT><<<gs, 32 * kScatterWarps, 0, s>>>(pos, col, mo, c->r_world ? world : nullptr, n, c->W, c->H,
                                                         c->ccur, bk, accept, c->dcount, dc);
+    // from here on the queues: wait until they are free, clear them if asked
+    if (queues_free && (e = cudaStreamWaitEvent(s, queues_free, 0)) != cudaSuccess) return e;
+    if (reset) {
+        static_assert(CNT_REJECTED == 0, "the rejected count comes first");
+        if ((e = cudaMemsetAsync(c->r_state, 0, sizeof(uint32_t) * P, s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(c->dcount + 1, 0, sizeof(unsigned long long) * (CNT_N - 1), s)) != cudaSuccess)
+            return e;
+        if (c->q_total && (e = cudaMemsetAsync(c->q_total, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
+    }
     // the cursors are spent: they take the queue states before the batch,
     // which every commit thread reads
     if ((e = cudaMemcpyAsync(c->ccur, c->r_state, sizeof(uint32_t) * P, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
@@ -443,15 +455,15 @@ cudaError_t launch_fifo_append(AfrContext *c, const AfrSampleBatch *batch, uint3
 }
 
 cudaError_t launch_ingest(AfrContext *c, const AfrSampleBatch *batch, uint32_t n, uint32_t seq0,
-                          cudaStream_t s) {
+                          cudaStream_t s, cudaEvent_t queues_free, bool reset) {
     const float4 *pos = reinterpret_cast<const float4 *>(batch->pos_dev);
     const float2 *mo = reinterpret_cast<const float2 *>(batch->motion_dev);
     const void *col = batch->color_dev;
     const float4 *world = reinterpret_cast<const float4 *>(batch->world_dev);
     switch (c->ct) {
-        case AFR_F32: return run<AFR_F32>(c, pos, col, mo, world, n, seq0, s);
-        case AFR_F16: return run<AFR_F16>(c, pos, col, mo, world, n, seq0, s);
-        default: return run<AFR_BF16>(c, pos, col, mo, world, n, seq0, s);
+        case AFR_F32: return run<AFR_F32>(c, pos, col, mo, world, n, seq0, s, queues_free, reset);
+        case AFR_F16: return run<AFR_F16>(c, pos, col, mo, world, n, seq0, s, queues_free, reset);
+        default: return run<AFR_BF16>(c, pos, col, mo, world, n, seq0, s, queues_free, reset);
     }
 }
 

@@ -408,6 +408,97 @@ def test_pipelined_steps_match_serial(dev):
         assert torch.equal(img, img_w) and torch.equal(tiles, tiles_w)
 
 
+def test_pipelined_binning_matches_serial(dev):
+    """afr_insert_samples_ex with the reset flag and refresh()'s reads_done
+    event: the next batch's binning starts at once, beside the current
+    image's gradients and reprojection, and only its reset and commit wait
+    for the event. Every image, tile record and counter equals the calls in
+    series; the buffers change every step and a batch carries rejected
+    samples."""
+    from paper_2510_15876_gb300.api import to_device_batch
+    W, H, b = 640, 360, 8
+    batches = []
+    for seed in range(4):
+        _, bt = _scene_batch("c4_512x512x8", seed=seed, n=W * H * b, W=W, H=H, b=b, speed=24.0 + 8 * seed)
+        if seed == 2:
+            bt["pos"][::97, 0] = np.nan
+            bt["color"][5::89, 1] = np.inf
+        batches.append(to_device_batch(bt, dev))
+    a, s = _mk(dev, W, H, b), _mk(dev, W, H, b)
+    want = []
+    for pos, col, mo in batches:
+        s.reset()
+        s.insert(pos, col, mo)
+        s.estimate_gradients(T_NOW)
+        s.reproject(T_NOW)
+        want.append((s.reconstruct(T_NOW), s.tile_feedback(), s.query()))
+    main, ingest = torch.cuda.current_stream(), torch.cuda.Stream(dev)
+    reads_done, ingested = torch.cuda.Event(), torch.cuda.Event()
+    reads_done.record(main)
+    got = []
+    for pos, col, mo in batches:
+        a.insert(pos, col, mo, stream=ingest, reset=True, queues_free=reads_done)
+        ingested.record(ingest)
+        main.wait_event(ingested)
+        img, tiles = a.refresh(T_NOW, reads_done=reads_done)
+        torch.cuda.synchronize()
+        got.append((img.clone(), tiles.clone(), a.query()))
+    for (img, tiles, q), (img_w, tiles_w, q_w) in zip(got, want):
+        assert torch.equal(img, img_w) and torch.equal(tiles, tiles_w)
+        assert q == q_w
+
+
+@pytest.mark.parametrize("kind", ["queues", "fifo", "world"])
+def test_insert_ex_equals_reset_and_insert(dev, kind):
+    """afr_insert_samples_ex(AFR_INSERT_RESET, event recorded on another
+    stream) leaves the per-pixel queues (or the reconstructor queue, or the
+    hit points) exactly as afr_reset followed by afr_insert_samples, after a
+    first batch filled them; unknown flags are refused."""
+    from paper_2510_15876_gb300 import _lib as L
+    W, H, b = 131, 67, 8
+    rng = np.random.default_rng(7)
+    kw = {"fifo_capacity": 3 * W * H} if kind == "fifo" else ({"world_points": True} if kind == "world" else {})
+    a, s = _mk(dev, W, H, b, **kw), _mk(dev, W, H, b, **kw)
+
+    def dev_batch(seed):
+        bt = _random_batch(np.random.default_rng(seed), 30000, W, H, bad=0.05)
+        t = [torch.from_numpy(bt[k]).to(dev) for k in ("pos", "color", "motion")]
+        wp = torch.from_numpy(rng.uniform(-1, 1, (30000, 4)).astype(np.float32)).to(dev) if kind == "world" else None
+        return t, wp
+
+    (p1, c1, m1), w1 = dev_batch(1)
+    (p2, c2, m2), w2 = dev_batch(2)
+    for r in (a, s):
+        r.insert(p1, c1, m1, world=w1)
+    s.reset()
+    s.insert(p2, c2, m2, world=w2)
+    side = torch.cuda.Stream(dev)
+    ev = torch.cuda.Event()
+    with torch.cuda.stream(side):
+        torch.cuda._sleep(1000000)   # the queues stay busy for a while on the other stream
+        ev.record(side)
+    a.insert(p2, c2, m2, world=w2, reset=True, queues_free=ev)
+    torch.cuda.synchronize()
+    for x, y in zip(a.export_ring(), s.export_ring()):
+        np.testing.assert_array_equal(x, y)
+    if kind == "world":   # the frame view from the stored hit points
+        vp = np.eye(4, dtype=np.float32)
+        vp[3, 2] = 1.0
+        vp[3, 3] = 2.0
+        a.reproject_camera(T_NOW, vp)
+        s.reproject_camera(T_NOW, vp)
+    else:                 # from the queues, or from the reconstructor queue
+        a.reproject(T_NOW)
+        s.reproject(T_NOW)
+    torch.cuda.synchronize()
+    for x, y in zip(a.export_frame(), s.export_frame()):
+        np.testing.assert_array_equal(x, y)
+    assert a.query() == s.query()
+    batch = L.AfrSampleBatch(p2.data_ptr(), c2.data_ptr(), m2.data_ptr(), None if w2 is None else w2.data_ptr())
+    import ctypes
+    assert a.lib.afr_insert_samples_ex(a.h, ctypes.byref(batch), 30000, 2, None, None) == L.AFR_ERR_INVALID_ARG
+
+
 # ----------------------------------------------------------------------------- end to end
 @pytest.mark.parametrize("key", ["c1_128x128x4", "c4_512x512x8", "c2_1024x1024x8"])
 def test_end_to_end_matches_oracle(dev, key):
