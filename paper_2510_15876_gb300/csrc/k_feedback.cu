@@ -65,9 +65,8 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(int W, int H, int S, i
 // slot's time beside its pixel's queue state (a warp reads 128 contiguous
 // bytes of times) so that the loads of successive rows overlap. Ages are
 // summed in FP32 over at most 32 rows of one slot column (32 ages, each at
-// most the window); those sums are added in FP64, per thread and by a tree
-// over the block. (The same kernel with FP32 there measured 126 against 54
-// microseconds at 1920x1080x16; the FP64 adds are a few per thread.)
+// most the window); those sums are added as double-float values (TwoSum
+// additions), per thread and by a tree over the block.
 struct alignas(16) TileTerm {
     float v;           // luminance variance
     float o;           // occluded share of the tile's slots
@@ -76,19 +75,19 @@ struct alignas(16) TileTerm {
     float sg, sgt;     // spatial and temporal gradient sums over non-empty pixels
     uint32_t empty, nonempty, has_samples, pad[3];
 };
-static_assert(sizeof(TileTerm) <= 8 * sizeof(double), "fits the 64 bytes a tile the context holds");
+static_assert(sizeof(TileTerm) <= 64, "fits the 64 bytes a tile the context holds");
 
 __global__ void __launch_bounds__(256) k_tile_terms(int W, int H, int S, int ntx, int b, float t_now,
                                                     const uint32_t *__restrict__ state, const float *__restrict__ r_t,
                                                     const TilePartial *__restrict__ tiles,
                                                     const uint32_t *__restrict__ occluded,
                                                     TileTerm *__restrict__ terms) {
-    __shared__ double sh[8];
+    __shared__ float2 sh[8];
     const int tile = blockIdx.x;
     const int x0 = (tile % ntx) * S, y0 = (tile / ntx) * S;
     const int tw = min(S, W - x0), th = min(S, H - y0);
     const int row_slots = tw * b;
-    double d = 0.0;
+    dfloat d{0.f, 0.f};   // double-float: each chunk's FP32 sum added exactly (TwoSum)
     for (int k = threadIdx.x; k < row_slots; k += blockDim.x) {
         const int px = k / b, sl = k - px * b;
         const size_t p0 = (size_t)y0 * W + x0 + px;
@@ -105,18 +104,21 @@ __global__ void __launch_bounds__(256) k_tile_terms(int W, int H, int S, int ntx
                 const float a = t_now - t;
                 acc += (age_rank < (int)(st & 0xFFFFu) && a > 0.f) ? a : 0.f;
             }
-            d += (double)acc;
+            d = df_add(d, dfloat{acc, 0.f});
         }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = d;
+    for (int o = 16; o > 0; o >>= 1)
+        d = df_add(d, dfloat{__shfl_xor_sync(0xffffffffu, d.h, o), __shfl_xor_sync(0xffffffffu, d.l, o)});
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = make_float2(d.h, d.l);
     __syncthreads();
     if (threadIdx.x < 32) {
-        double xd = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+        const float2 v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : make_float2(0.f, 0.f);
+        dfloat xd{v.x, v.y};
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) xd += __shfl_xor_sync(0xffffffffu, xd, o);
-        const float x = (float)xd;
+        for (int o = 16; o > 0; o >>= 1)
+            xd = df_add(xd, dfloat{__shfl_xor_sync(0xffffffffu, xd.h, o), __shfl_xor_sync(0xffffffffu, xd.l, o)});
+        const float x = __fadd_rn(xd.h, xd.l);
         if (threadIdx.x == 0) {
             const TilePartial tp = tiles[tile];
             const uint32_t slots = (uint32_t)(tw * th) * (uint32_t)b, empty = slots - tp.n;
