@@ -12,10 +12,12 @@
 //  3. scatter: each sample appends its 64-byte record (position, colour,
 //              motion, batch index, hit point) to its pixel's bucket. A warp
 //              stages its 32 records in shared memory and stores each with
-//              four lanes, so every store is two whole sectors; a thread takes
-//              the tickets of both its samples before using either. A sample
-//              whose colour or motion is not finite leaves a dead record
-//              (batch index kInvalid).
+//              four lanes, so every store is two whole sectors. The pixel's
+//              append cursor starts at the bucket's offset, so the ticket its
+//              atomic returns is the record's place; a thread takes the tickets
+//              of both its samples before using either. A sample whose colour
+//              or motion is not finite leaves a dead record (batch index
+//              kInvalid).
 //  4. commit:  a thread per bucket record, in bucket (= pixel) order: its
 //              rank among its pixel's live records is the number of them with
 //              a smaller batch index (read from shared memory, where a block

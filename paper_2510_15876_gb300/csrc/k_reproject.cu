@@ -9,7 +9,8 @@
 //  scan:   bin offsets.
 //  list:   each moved sample (its bin kept by the count pass, 4 bytes a
 //          slot) writes its slot index and its sequence number into its bin's
-//          lists (unordered, 8 bytes a sample).
+//          lists (unordered, 8 bytes a sample), at the ticket its bin's cursor
+//          returns (the cursors start at the bin offsets).
 //  place:  thread per frame record, in bin order: the slot of list entry e
 //          is moved again, its rank in the bin is the number of sequence
 //          numbers in the bin's list below its own (sequence numbers are
