@@ -71,3 +71,19 @@ def test_pairs_of_matches_brute_force(R):
                     if dx * dx + dy * dy <= R * R and 0 <= x + dx < W and 0 <= y + dy < H:
                         ref += int(c[y + dy, x + dx])
     assert bench.pairs_of(off, W, H, R) == ref
+
+
+def test_filter_traffic_only_for_the_captured_source(monkeypatch):
+    """roofline.traffic: a figure on the command line wins; the recorded
+    capture is reported only for the captured workload and colour type and
+    only while the filter's sources hash to the captured ones."""
+    import types
+    import bench
+    args = types.SimpleNamespace(filter_traffic=None, workload=bench.WORKLOAD)
+    assert bench.filter_traffic(types.SimpleNamespace(filter_traffic=5.0, workload="x"), "f16") == (5.0, "--filter-traffic")
+    assert bench.filter_traffic(args, "f16")[0] is None
+    assert bench.filter_traffic(types.SimpleNamespace(filter_traffic=None, workload="c1_128x128x4"), "f32")[0] is None
+    value, _ = bench.filter_traffic(args, "f32")
+    assert value is not None and value > 0   # the sources in the tree are the captured ones
+    monkeypatch.setattr(bench, "FILTER_TRAFFIC", {("0" * 64, "0" * 64): 1.0})
+    assert bench.filter_traffic(args, "f32") == (None, "kernel source changed since the last capture")
