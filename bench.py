@@ -43,7 +43,7 @@ METRIC = "1080p reconstructions/s (16-deep buffer)"
 T_NOW = 1.0
 # kernels launched per call of the step (memsets and copies excluded), as the
 # launch sequences in csrc/ issue them
-LAUNCHES = {"ingest": 6, "gradients": 2, "reproject": 7, "reconstruct": 2, "feedback": 1}
+LAUNCHES = {"ingest": 7, "gradients": 2, "reproject": 7, "reconstruct": 2, "feedback": 1}
 STAGES = ["ingest", "gradients", "reproject", "reconstruct", "feedback"]
 
 
