@@ -81,3 +81,17 @@ def test_debug_library_exports_its_hooks(lib):
         assert hasattr(dbg, n), n
     for n in hooks:
         assert not hasattr(lib, n), n
+
+
+def test_null_handles_are_rejected_on_host(lib):
+    """Every call that takes a context or a batch refuses a null one before
+    touching the GPU (no device needed)."""
+    from paper_2510_15876_gb300 import _lib as L
+    prm = L.AfrParams(1, 0, 3, 1, 0, 1)
+    assert lib.afr_insert_samples(None, None, 1, None) == L.AFR_ERR_INVALID_ARG
+    assert lib.afr_insert_samples_ex(None, None, 1, 0, None, None) == L.AFR_ERR_INVALID_ARG
+    assert lib.afr_insert_samples_ex(None, None, 0, L.AFR_INSERT_RESET, None, None) == L.AFR_ERR_INVALID_ARG
+    assert lib.afr_estimate_gradients(None, 1.0, None) == L.AFR_ERR_INVALID_ARG
+    assert lib.afr_reproject(None, 1.0, None) == L.AFR_ERR_INVALID_ARG
+    assert lib.afr_batch_refresh(None, 1.0, ctypes.byref(prm), None, None) == L.AFR_ERR_INVALID_ARG
+    assert lib.afr_batch_reconstruct(None, 1.0, ctypes.byref(prm), None, None) == L.AFR_ERR_INVALID_ARG
